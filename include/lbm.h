@@ -1,0 +1,274 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the Purified
+ * Two-Relaxation-Time (P-TRT) lattice Boltzmann update of Yu et al.,
+ * arXiv 2602.06686, with the standard TRT and TRT-RLB comparators.
+ *
+ * What the library computes, per node and time step (a fused pull-stream +
+ * collide update):
+ *   f_i(x, t+1) = f*_i(x - e_i, t), or f*_ibar(x, t) when x - e_i is solid or
+ *   outside a non-periodic axis (halfway bounce-back, Sec. 3.3 and Sec. 3.4),
+ *   f* = f_eq + (1 - w+) R2 + (1 - w-) R3 + F_i/2 + (1 - w+/2) S+     (Eq. PTRT)
+ * with rho and the half-force velocity u of Eq. macro, the third-order
+ * equilibrium of Eq. feq, F_i = w_i e_i.F / cs^2, the symmetric Guo source
+ * S+ = w_i [(e_i.u)(e_i.F)/cs^4 - u.F/cs^2] (Eq. source_guo) and
+ *   P-TRT    R2 = fneq+ - P_G fneq (ghost subtraction, Thm 2nd), R3 = fneq- + F_i/2 (Eq. R3_force)
+ *   TRT      R2 = fneq+,                                         R3 = fneq- + F_i/2
+ *   TRT-RLB  R2, R3 = orthogonal projections of fneq onto span{H2}, span{H3} (Eq. R2R3_hermite)
+ *   BGK      TRT with w- = w+;  RLB: P-TRT with w- = 1 (second-order regularised, single rate).
+ * The force term "F_i/2 + (1-w-) (fneq- + F_i/2)" is the reading under which the
+ * update conserves mass exactly and adds the impulse F (Eq. macro): Eq. PTRT as
+ * printed omits the first-order term (1 - w+) R1 and Scheme I attaches -u.F/cs^2
+ * to tau_s2.  On D3Q19 the ghost subspace is the orthogonal complement of
+ * span{1, H2} in the symmetric subspace (the printed App. A.2 products are not
+ * orthogonal).
+ *
+ * Rates: tau+ = 1/2 + nu/cs^2 (Eq. viscosity), tau- = 1/2 + Lambda/(tau+ - 1/2)
+ * (Sec. 3.2, magic parameter Lambda_s).  cs^2 = 1/3.
+ *
+ * Lattices and population order:
+ *   D2Q9  (Eq. D2Q9): 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1),
+ *         6 (-1,1), 7 (-1,-1), 8 (1,-1); w = 4/9, 1/9, 1/36.
+ *   D3Q19 (App. A.2, order not printed): 0 rest; 1..6 = +x,-x,+y,-y,+z,-z;
+ *         7..10 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); 11..14 = (1,0,1),(-1,0,-1),
+ *         (1,0,-1),(-1,0,1); 15..18 = (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);
+ *         w = 1/3, 1/18, 1/36.
+ *
+ * Conventions common to every call:
+ *   - Device buffers are allocated by the caller and borrowed by the library
+ *     (bound with lbm_bind_buffers); the library never allocates device memory.
+ *     It allocates only its host-side context.
+ *   - "device" pointers must be addresses in the current CUDA device's memory
+ *     (or managed memory); "host" pointers are ordinary host memory.
+ *   - Field layout: scalar fields are [nz][ny][nx] (x fastest, no padding),
+ *     vector fields are D consecutive scalar fields (component planes), and
+ *     decoded populations are Q consecutive scalar fields, all FP64.
+ *   - All work is enqueued on the stream given to lbm_create, asynchronously,
+ *     unless a call says it synchronises.
+ *   - Return value: LBM_OK (0) or a negative LBM_ERR_* code; nothing is thrown
+ *     across the ABI and nothing exits the process.  lbm_strerror names a code.
+ *   - The time level: after lbm_init_equilibrium / lbm_set_populations and any
+ *     number of lbm_step calls, lbm_macros and lbm_get_populations describe the
+ *     pre-collision state f(x, t).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)         /* invalid argument, size or pointer */
+#define LBM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define LBM_ERR_DIVERGED (-3)    /* NaN/Inf, rho <= 0 or |u| > 1 seen in an update */
+#define LBM_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define LBM_ERR_UNSUPPORTED (-5) /* valid but not implemented combination */
+#define LBM_ERR_STATE (-6)       /* call out of order (e.g. buffers not bound) */
+#define LBM_ERR_ALIGN (-7)       /* a buffer is not 256-byte aligned */
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+typedef enum {
+  LBM_TRT = 0,
+  LBM_TRT_RLB = 1,
+  LBM_P_TRT = 2,
+  LBM_BGK = 3,
+  LBM_RLB = 4
+} lbm_collision;
+/* Storage of populations.  Every format stores the shifted value
+ * df_i = f_i - w_i rho0 (round to nearest even); FP16/BF16 keep gradual
+ * underflow.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise. */
+typedef enum {
+  LBM_F64 = 0,
+  LBM_F32 = 1,
+  LBM_F16_SHIFTED = 2,
+  LBM_BF16_SHIFTED = 3
+} lbm_storage;
+/* A/B: two buffers, read one, write the other.  AA: one buffer updated in place,
+ * even steps local, odd steps neighbour-wise (halves the memory). */
+typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
+
+typedef struct {
+  int lattice;           /* lbm_lattice */
+  int nx, ny, nz;        /* lattice extent; nz = 1 for D2Q9 */
+  double nu;             /* kinematic viscosity; or 0 and tau_plus > 0 */
+  double tau_plus;       /* tau_s1; or 0 and nu > 0 */
+  double Lambda;         /* magic parameter Lambda_s; or 0 and tau_minus > 0 */
+  double tau_minus;      /* tau_s2; or 0 and Lambda > 0 */
+  int collision;         /* lbm_collision */
+  double force[3];       /* uniform body force (lattice units) */
+  double rho0;           /* reference density of the shifted storage (e.g. 1) */
+  int periodic[3];       /* 1 = periodic axis; 0 = halfway bounce-back walls just
+                            outside the first and last node of that axis */
+  int storage;           /* lbm_storage */
+  int layout;            /* lbm_layout */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Library version, e.g. 100 for 1.0.0. */
+int lbm_version(void);
+
+/* Static description of an error code (never NULL). */
+const char* lbm_strerror(int code);
+
+/* Byte sizes of the buffers a lattice needs: *pop_bytes for ONE population
+ * buffer (A/B layout needs two, AA one) and *scratch_bytes for the scratch
+ * buffer (diagnostics, host staging, status words).  Either output may be NULL.
+ * Returns LBM_ERR_ARG for invalid parameters. */
+int lbm_buffer_sizes(const lbm_params* p, size_t* pop_bytes, size_t* scratch_bytes);
+
+/* Validates parameters, derives the rates and creates a context that enqueues
+ * on `cuda_stream` (a cudaStream_t; NULL = legacy default stream) on the
+ * current device.  The context is not usable for compute until buffers are
+ * bound.  *out receives the context (owned by the caller; lbm_destroy frees). */
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
+
+/* Binds caller-owned device buffers, all 256-byte aligned:
+ *   pop_a, pop_b  population buffers of lbm_buffer_sizes' pop_bytes each
+ *                 (pop_b must be NULL for the AA layout);
+ *   solid_mask    uint8 [nz][ny][nx], nonzero = solid node, or NULL for none;
+ *                 it is read at every step and must stay valid while bound;
+ *   scratch       scratch_bytes of device memory.
+ * The buffers must not overlap.  No data is read or written by this call. */
+int lbm_bind_buffers(lbm_ctx* ctx, void* pop_a, void* pop_b, const uint8_t* solid_mask,
+                     void* scratch);
+
+/* Sets the state to the equilibrium f = f_eq(rho, u) (Eq. feq) and the step
+ * counter to 0.  rho: device FP64 [N]; u: device FP64 [D][N]. */
+int lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u);
+
+/* As lbm_init_equilibrium with HOST inputs; copies them through the scratch
+ * buffer and synchronises the stream before returning. */
+int lbm_init_equilibrium_host(lbm_ctx* ctx, const double* rho, const double* u);
+
+/* Advances n >= 0 time steps (the hot path).  Asynchronous; returns launch
+ * status only.  Divergence is recorded on the device and reported by
+ * lbm_status / lbm_diagnostics. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Density and half-force velocity (Eq. macro) of the current pre-collision
+ * state into device FP64 buffers rho [N] and u [D][N].  Solid nodes get rho0, 0. */
+int lbm_macros(lbm_ctx* ctx, double* rho, double* u);
+
+/* As lbm_macros into HOST buffers; synchronises the stream. */
+int lbm_macros_host(lbm_ctx* ctx, double* rho, double* u);
+
+/* Decoded FP64 pre-collision populations f [Q][N] (device).  Solid nodes: w_i rho0. */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+
+/* Replaces the state by the FP64 pre-collision populations f [Q][N] (device),
+ * encoded to the storage format.  Values at solid nodes are ignored. */
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* FP64 diagnostics of the current state over fluid nodes, synchronising:
+ *   out[0] mass sum rho, out[1..3] momentum sum rho u, out[4] kinetic energy
+ *   1/2 sum rho |u|^2, out[5] enstrophy 1/2 sum |curl u|^2 with second-order
+ *   central differences (a neighbour across a periodic axis wraps; across a
+ *   non-periodic edge or on a solid node it counts as u = 0), out[6] 1 if any
+ *   rho or u is not finite or rho <= 0, out[7] the step counter. */
+int lbm_diagnostics(lbm_ctx* ctx, double out[8]);
+
+/* Relative L2 error (Sec. 3) of the current velocity against u_ref (device
+ * FP64 [D][N]) over fluid nodes: sqrt(sum |u - u_ref|^2 / sum |u_ref|^2).
+ * Synchronises. */
+int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
+
+/* Synchronises the stream and reports LBM_ERR_DIVERGED if any update since the
+ * last lbm_init_equilibrium / lbm_set_populations met NaN/Inf, rho <= 0 or
+ * |u| > 1; *first_step (may be NULL) receives the earliest such step or -1. */
+int lbm_status(lbm_ctx* ctx, long long* first_step);
+
+/* Number of completed time steps since initialisation. */
+int lbm_step_count(const lbm_ctx* ctx, long long* t);
+
+/* Raw checkpoint of the state: copies the buffer that holds the current state
+ * (pop_bytes, storage format, layout-dependent) to `dst` (device) and returns the
+ * step counter in *t.  lbm_restore copies such a snapshot back and sets the step
+ * counter, so that a resumed run is bit-identical to an uninterrupted one.
+ * Both are asynchronous on the context's stream. */
+int lbm_checkpoint(lbm_ctx* ctx, void* dst, size_t bytes, long long* t);
+int lbm_restore(lbm_ctx* ctx, const void* src, size_t bytes, long long t);
+
+/* Number of kernels this context has enqueued since creation (all entry points). */
+int lbm_launch_count(const lbm_ctx* ctx, long long* launches);
+
+/* Text of the most recent error raised in the calling thread (CUDA error name
+ * and the call that failed), or "" if none. */
+const char* lbm_last_error(void);
+
+/* Kernel variants (nodes per thread, block shape) available for this context,
+ * their names, the selected one, and selection by index. */
+int lbm_variant_count(const lbm_ctx* ctx, int* n);
+int lbm_variant_name(const lbm_ctx* ctx, int v, char* buf, size_t len);
+int lbm_get_variant(const lbm_ctx* ctx, int* v);
+int lbm_set_variant(lbm_ctx* ctx, int v);
+
+/* Times every variant (reps steps each, CUDA events, after one warm-up) and
+ * selects the fastest; *chosen (may be NULL) receives it, times_ms (may be
+ * NULL, length lbm_variant_count) the per-step times.  The state is not
+ * changed: trial steps read the current buffer and write the other one, which
+ * the next step overwrites.  A/B layout only (AA returns LBM_ERR_UNSUPPORTED).
+ * Results are cached per (lattice, storage, collision, mask, extent) for the
+ * process.  Synchronises. */
+int lbm_autotune(lbm_ctx* ctx, int reps, int* chosen, float* times_ms);
+
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Streaming copy kernel (128-bit loads/stores, grid-stride) of `bytes` from
+ * src to dst (device, 16-byte aligned, bytes a multiple of 16) on a stream: the
+ * measured copy ceiling for the bandwidth roofline. */
+int lbm_copy_ceiling(const void* src, void* dst, size_t bytes, void* cuda_stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent lattices stepped together by ONE persistent kernel (one
+ * cooperative launch for all steps, a bounded grid barrier between steps),
+ * replayed from a CUDA graph.  All lattices share lattice, collision,
+ * storage and layout (A/B); extents, rates and forces are per lattice.
+ */
+typedef struct lbm_batch lbm_batch;
+
+/* Per-lattice population offsets are packed in lattice order; *pop_bytes is the
+ * size of ONE arena (two are needed), *scratch_bytes of the scratch buffer. */
+int lbm_batch_buffer_sizes(int n, const lbm_params* p, size_t* pop_bytes, size_t* scratch_bytes);
+
+int lbm_batch_create(int n, const lbm_params* p, void* cuda_stream, lbm_batch** out);
+
+/* Binds the two population arenas and the scratch buffer (device, 256-byte aligned). */
+int lbm_batch_bind(lbm_batch* b, void* pop_a, void* pop_b, void* scratch);
+
+/* A context that views lattice i of the batch (its slice of the arenas and the
+ * shared scratch): lbm_init_equilibrium, lbm_macros, lbm_get_populations,
+ * lbm_diagnostics ... work on it.  Owned by the batch; do not destroy it and
+ * do not lbm_step it (lbm_batch_step advances every view). */
+int lbm_batch_lattice(lbm_batch* b, int i, lbm_ctx** view);
+
+/* Advances every lattice by n steps.  mode 0: the persistent cooperative kernel
+ * captured once per n in a CUDA graph and replayed; mode 1: one ordinary launch
+ * per lattice per step (the sequential baseline).  Returns LBM_ERR_TIMEOUT if a
+ * grid barrier gave up (the state is then undefined), after synchronising. */
+int lbm_batch_step(lbm_batch* b, int n, int mode);
+
+/* Tile shape of the persistent kernel (rows x nodes-per-row of one tile),
+ * variants and the autotuner, as for single lattices (mode-0 timing). */
+int lbm_batch_variant_count(const lbm_batch* b, int* n);
+int lbm_batch_variant_name(const lbm_batch* b, int v, char* buf, size_t len);
+int lbm_batch_set_variant(lbm_batch* b, int v);
+int lbm_batch_autotune(lbm_batch* b, int steps, int* chosen, float* times_ms);
+
+/* Grid-barrier wait limit in seconds (default 2.0).  For tests: `extra` > 0
+ * makes each barrier wait for `extra` arrivals that never come, so the wait
+ * must run out and lbm_batch_step must return LBM_ERR_TIMEOUT. */
+int lbm_batch_set_barrier(lbm_batch* b, double timeout_s, int extra);
+
+/* Number of kernel launches the last lbm_batch_step enqueued. */
+int lbm_batch_launches(const lbm_batch* b, long long* launches);
+
+int lbm_batch_destroy(lbm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,106 @@
+// storage.cuh -- population storage formats and vectorised plane access.
+//
+// Every format stores the shifted population df_i = f_i - w_i rho0, so that the
+// stored magnitudes are the (small) deviations from the rest state: FP64 and
+// FP32 keep more significant digits of the flow signal, and FP16/BF16 become
+// usable at all.  Encoding rounds to nearest even; FP16 keeps subnormals.
+// Arithmetic type R is double for FP64 storage and float otherwise.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <cstring>
+
+namespace lbm {
+
+struct StF64 {
+  using T = double;
+  using R = double;
+  static constexpr int id = 0;
+  static constexpr int VBYTES = 16;
+  __device__ __forceinline__ static R dec(T v) { return v; }
+  __device__ __forceinline__ static T enc(R v) { return v; }
+};
+struct StF32 {
+  using T = float;
+  using R = float;
+  static constexpr int id = 1;
+  static constexpr int VBYTES = 16;
+  __device__ __forceinline__ static R dec(T v) { return v; }
+  __device__ __forceinline__ static T enc(R v) { return v; }
+};
+struct StF16 {
+  using T = __half;
+  using R = float;
+  static constexpr int id = 2;
+  static constexpr int VBYTES = 16;
+  __device__ __forceinline__ static R dec(T v) { return __half2float(v); }
+  __device__ __forceinline__ static T enc(R v) { return __float2half_rn(v); }
+};
+struct StBF16 {
+  using T = __nv_bfloat16;
+  using R = float;
+  static constexpr int id = 3;
+  static constexpr int VBYTES = 16;
+  __device__ __forceinline__ static R dec(T v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static T enc(R v) { return __float2bfloat16_rn(v); }
+};
+
+template <int BYTES>
+struct RawT;
+template <>
+struct RawT<1> {
+  using type = unsigned char;
+};
+template <>
+struct RawT<2> {
+  using type = unsigned short;
+};
+template <>
+struct RawT<4> {
+  using type = unsigned int;
+};
+template <>
+struct RawT<8> {
+  using type = uint2;
+};
+template <>
+struct RawT<16> {
+  using type = uint4;
+};
+
+__device__ __forceinline__ unsigned char ldg_raw(const unsigned char* p) { return __ldg(p); }
+__device__ __forceinline__ unsigned short ldg_raw(const unsigned short* p) { return __ldg(p); }
+__device__ __forceinline__ unsigned int ldg_raw(const unsigned int* p) { return __ldg(p); }
+__device__ __forceinline__ uint2 ldg_raw(const uint2* p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ldg_raw(const uint4* p) { return __ldg(p); }
+
+// NV consecutive elements starting at p (p aligned to NV * sizeof(T)).
+template <typename T, int NV>
+__device__ __forceinline__ void ld_vec(const T* p, T (&out)[NV]) {
+  using Raw = typename RawT<sizeof(T) * NV>::type;
+  Raw r = ldg_raw(reinterpret_cast<const Raw*>(p));
+  memcpy(out, &r, sizeof(Raw));
+}
+
+template <class S, int NV>
+__device__ __forceinline__ void ld_dec(const typename S::T* p, typename S::R (&out)[NV]) {
+  typename S::T t[NV];
+  ld_vec<typename S::T, NV>(p, t);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = S::dec(t[k]);
+}
+
+template <class S, int NV>
+__device__ __forceinline__ void st_enc(typename S::T* p, const typename S::R (&v)[NV]) {
+  using Raw = typename RawT<sizeof(typename S::T) * NV>::type;
+  typename S::T t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) t[k] = S::enc(v[k]);
+  Raw r;
+  memcpy(&r, t, sizeof(Raw));
+  *reinterpret_cast<Raw*>(p) = r;
+}
+
+}  // namespace lbm

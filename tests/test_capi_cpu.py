@@ -1,0 +1,72 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+declared in include/lbm.h, and its host-only calls (parameter validation,
+buffer plan, error strings) behave as documented.  No GPU compute is called."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_06686_gb300 import build, lbm
+    build.build()
+    return lbm.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2602_06686_gb300 import lbm
+    names = _declared()
+    assert len(names) >= 30
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbm.EXPORTED) == names
+
+
+def test_version_and_strerror(lib):
+    assert lib.lbm_version() >= 100
+    for code in range(0, -8, -1):
+        assert lib.lbm_strerror(code)
+    assert b"unknown" in lib.lbm_strerror(-99)
+
+
+def test_buffer_plan(lib):
+    from paper_2602_06686_gb300.lbm import buffer_sizes, make_params
+    pop, scr = buffer_sizes(make_params("D2Q9", 64, 64, nu=0.01, Lambda=0.25, storage="F64"))
+    assert pop == 9 * 64 * 64 * 8
+    pop, _ = buffer_sizes(make_params("D2Q9", 4096, 4096, nu=0.004, Lambda=0.25, storage="F32"))
+    assert pop == 9 * 4096 * 4096 * 4
+    # rows padded to 16 bytes, planes to 256 bytes
+    pop, _ = buffer_sizes(make_params("D3Q19", 30, 7, 5, nu=0.01, Lambda=0.25, storage="F16"))
+    plane = ((32 * 7 * 5 + 127) // 128) * 128
+    assert pop == 19 * plane * 2
+    _, scr = buffer_sizes(make_params("D3Q19", 10, 10, 10, nu=0.01, Lambda=0.25))
+    assert scr >= 4 * 1000 * 8
+
+
+@pytest.mark.parametrize("kw", [
+    dict(lattice="D2Q9", nx=8, ny=8, nz=2),
+    dict(lattice="D2Q9", nx=0, ny=8),
+    dict(lattice="D2Q9", nx=8, ny=8, tau_plus=0.8),          # nu and tau_plus both given
+    dict(lattice="D2Q9", nx=8, ny=8, Lambda=0.0),            # neither Lambda nor tau_minus
+    dict(lattice="D2Q9", nx=8, ny=8, collision=7),
+    dict(lattice="D2Q9", nx=8, ny=8, storage=9),
+    dict(lattice="D2Q9", nx=8, ny=8, rho0=0.0),
+    dict(lattice="D2Q9", nx=8, ny=8, force=(0, 0, 1e-3)),
+    dict(lattice="D2Q9", nx=8, ny=8, periodic=(2, 1, 1)),
+])
+def test_invalid_parameters_rejected(lib, kw):
+    from paper_2602_06686_gb300.lbm import LBMError, buffer_sizes, make_params
+    base = dict(nu=0.05, Lambda=0.25)
+    base.update(kw)
+    with pytest.raises(LBMError) as e:
+        buffer_sizes(make_params(**base))
+    assert e.value.code == -1
