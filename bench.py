@@ -6,7 +6,7 @@ diagnostics reduction (mass, momentum, kinetic energy, enstrophy, NaN flag).
 
 Workload (default): D2Q9 P-TRT double shear layer, 4096 x 4096 periodic, FP32
 shifted storage, U0 = 0.1, kappa = 80, delta = 0.05, Re = U0 N / nu = 1e5,
-Lambda = 1/4, A/B buffers (2 x 604 MB, far larger than the 129 MB L2, so no
+1/tau- = 1.6, A/B buffers (2 x 604 MB, far larger than the 129 MB L2, so no
 flush is needed between iterations).  Metric: MLUPS (million lattice-node
 updates per second, all nodes) and the fraction of the HBM roofline
 (72 bytes per D2Q9 FP32 node update) of the fused kernel.
@@ -172,7 +172,7 @@ def oracle_sample(seconds_target: float = 12.0, n: int = 512, threads: int | Non
     import workloads as W
     threads = threads or len(os.sched_getaffinity(0))
     nu = 0.1 * n / 1e5
-    wp, wm = O.rates(nu=nu, Lambda=0.25)
+    wp, wm = O.rates(nu=nu, tau_minus=1 / 1.6)
     p = O.Params(O.D2Q9, n, n, 1, collision=O.P_TRT, omega_plus=wp, omega_minus=wm)
     rho, u = W.double_shear(n)
     f = O.init_equilibrium(p, rho, u)
@@ -197,7 +197,7 @@ def run_reference(args):
     threads = len(os.sched_getaffinity(0))
     n = 512
     nu = 0.1 * n / 1e5
-    wp, wm = O.rates(nu=nu, Lambda=0.25)
+    wp, wm = O.rates(nu=nu, tau_minus=1 / 1.6)
     p = O.Params(O.D2Q9, n, n, 1, collision=O.P_TRT, omega_plus=wp, omega_minus=wm)
     rho, u = W.double_shear(n)
     f = O.init_equilibrium(p, rho, u)
@@ -238,7 +238,8 @@ def workload_fields(kind: str, n: int):
 def make_lattice(lat: str, n: int, storage: str, collision: str = "P_TRT"):
     from paper_2602_06686_gb300 import Lattice
     if lat == "D2Q9":
-        return Lattice(lattice="D2Q9", nx=n, ny=n, nz=1, nu=0.1 * n / 1e5, Lambda=0.25,
+        # double shear layer: Re = U0 N / nu = 1e5, 1/tau- = 1.6 (the stability optimum of Sec. 3.1)
+        return Lattice(lattice="D2Q9", nx=n, ny=n, nz=1, nu=0.1 * n / 1e5, tau_minus=1 / 1.6,
                        collision=collision, storage=storage)
     return Lattice(lattice="D3Q19", nx=n, ny=n, nz=n, nu=0.05 * n / (2 * math.pi * 1600),
                    Lambda=0.25, collision=collision, storage=storage)
@@ -276,6 +277,48 @@ def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision=
     rc, _ = g.status()
     out["diverged"] = rc != 0
     del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched(peak: float, count: int = 256, steps: int = 500):
+    """256 uneven D2Q9 P-TRT double shear lattices (side lengths U{64..1024}, Re
+    log-uniform in [1e3, 1e7], Lambda in {1/12, 3/16, 1/4}, seeded), FP32, advanced
+    `steps` steps by the persistent kernel in a CUDA graph versus one launch per
+    lattice per step."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Batch
+    specs = []
+    for d in W.batch_lattices(count):
+        specs.append(dict(lattice="D2Q9", nx=d["nx"], ny=d["ny"], nu=0.1 * d["nx"] / d["Re"],
+                          Lambda=d["Lambda"], collision="P_TRT", storage="F32"))
+    b = Batch(specs)
+
+    def init():
+        for i, s in enumerate(specs):
+            b.lattice(i).init_equilibrium(*W.double_shear_rect(s["nx"], s["ny"]))
+
+    init()
+    chosen, _ = b.autotune(steps=4)
+    out = {"lattices": count, "nodes": b.nodes, "steps": steps,
+           "tile": b.variants()[chosen]}
+    for mode, name in ((0, "persistent_graph"), (1, "sequential_launches")):
+        init()
+        b.step(2, mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(steps, mode)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"mlups": b.nodes * steps / dt / 1e6, "seconds": dt,
+                     "launches": b.launches}
+    out["frac_persistent"] = out["persistent_graph"]["mlups"] * 1e6 * 72 / 1e9 / peak
+    out["speedup_vs_sequential"] = (out["persistent_graph"]["mlups"]
+                                    / out["sequential_launches"]["mlups"])
+    out["diverged"] = [i for i in range(count) if b.lattice(i).status()[0] != 0]
+    b.close()
+    del b
     torch.cuda.empty_cache()
     return out
 
@@ -336,6 +379,7 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     launches = g.launches - launches0
+    rc, first = g.status()
     total_s = t_start.elapsed_time(t_end) * 1e-3
     kernel_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / (args.steps * inner)
     units = float(N) * inner * args.steps
@@ -368,7 +412,6 @@ def run_ours(args):
     bpn = BYTES_PER_NODE[("D2Q9", "F32")]
     achieved = bpn * N / kernel_s / 1e9
     khash = csrc_hash()
-    rc, first = g.status()
     extra = {}
     if rank == 0 and not args.no_extra:
         del g
@@ -382,6 +425,7 @@ def run_ours(args):
         extra["d3q19_trt_rlb_f32"] = secondary("D3Q19", 384, "F32", "taylor_green_3d", peak,
                                                "TRT_RLB")
         extra["d3q19_f64"] = secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)
+        extra["batch256"] = batched(peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
@@ -393,7 +437,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"D2Q9 P-TRT double shear layer {n}x{n}, FP32 shifted storage, "
-                               f"Re=1e5, Lambda=1/4, A/B buffers",
+                               f"Re=1e5, 1/tau-=1.6, A/B buffers",
                    "updates_per_step": inner, "diagnostics_per_step": 1,
                    "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
                    "variant": variant, "parallelism": f"replicas x{world}"},

@@ -152,6 +152,7 @@ struct lbm_ctx {
   void* pop[2] = {nullptr, nullptr};
   const uint8_t* mask = nullptr;
   char* scratch = nullptr;
+  unsigned int* flag = nullptr;  // divergence flag (own scratch, or the batch's per-lattice slot)
   bool bound = false;
   bool view = false;  // owned by a batch
   int cur = 0;        // A/B: index of the buffer holding the state
@@ -163,7 +164,7 @@ struct lbm_ctx {
 
 namespace lbm {
 
-unsigned int* flag_ptr(lbm_ctx* c) { return reinterpret_cast<unsigned int*>(c->scratch + kFlagOffset); }
+unsigned int* flag_ptr(lbm_ctx* c) { return c->flag; }
 
 AuxLaunch aux_of(lbm_ctx* c) {
   AuxLaunch a{};
@@ -222,6 +223,7 @@ int ctx_bind(lbm_ctx* c, void* a, void* b, const uint8_t* mask, void* scratch) {
   c->pop[1] = b;
   c->mask = mask;
   c->scratch = static_cast<char*>(scratch);
+  c->flag = reinterpret_cast<unsigned int*>(c->scratch + kFlagOffset);
   c->bound = true;
   c->cur = 0;
   c->t = 0;
@@ -254,6 +256,13 @@ void ctx_get_state(const lbm_ctx* c, int* cur, long long* t) {
   *t = c->t;
 }
 void ctx_mark_view(lbm_ctx* c) { c->view = true; }
+void ctx_set_flag(lbm_ctx* c, unsigned int* flag) { c->flag = flag; }
+cudaStream_t ctx_stream(const lbm_ctx* c) { return c->stream; }
+const Ops* ctx_ops(const lbm_ctx* c) { return c->ops; }
+const std::vector<Variant>& ctx_variants(const lbm_ctx* c) { return c->vars; }
+int ctx_variant(const lbm_ctx* c) { return c->var; }
+StepLaunch ctx_step_launch(lbm_ctx* c, const Variant& v) { return step_of(c, v); }
+void ctx_delete(lbm_ctx* c) { delete c; }
 void ctx_add_launches(lbm_ctx* c, long long n) { c->launches += n; }
 int ctx_fail(int code, const char* what) { return fail(code, what); }
 
@@ -589,6 +598,7 @@ int lbm_destroy(lbm_ctx* c) {
   delete c;
   return LBM_OK;
 }
+
 
 int lbm_copy_ceiling(const void* src, void* dst, size_t bytes, void* cuda_stream) {
   if (!src || !dst || (bytes % 16) != 0 || (reinterpret_cast<uintptr_t>(src) & 15) ||

@@ -44,6 +44,33 @@ struct AuxLaunch {
   cudaStream_t stream;
 };
 
+// Per-lattice descriptor and tile of the persistent batched kernel.
+struct BatchDesc {
+  GeoH g;
+  double rho0, cp, cm, hg, F[3];
+  long long off;  // byte offset of the lattice in each population arena
+};
+struct BatchTile {
+  int lat, x0, y0, z;
+};
+struct BatchLaunch {
+  const BatchDesc* desc;
+  const BatchTile* tiles;
+  int ntiles;
+  char* A;
+  char* B;
+  int nsteps;
+  int parity0;          // 0: state in A, 1: state in B
+  unsigned int step0;   // index of the first step (divergence records)
+  unsigned int* flags;  // per-lattice divergence flags
+  void* bar;            // BarrierWords
+  unsigned int expected;
+  long long timeout_ns;
+  int collision;
+  int bx, by, blocks;
+  cudaStream_t stream;
+};
+
 struct Ops {
   int Q, D, esize;
   // vector widths this storage supports for the fused kernel
@@ -54,6 +81,9 @@ struct Ops {
   cudaError_t (*set_pop)(const AuxLaunch&, const double* f);
   cudaError_t (*get_pop)(const AuxLaunch&, double* f);
   cudaError_t (*macros)(const AuxLaunch&, double* rho, double* u);
+  // persistent batched kernel (cooperative launch) and its occupancy
+  cudaError_t (*batch)(const BatchLaunch&);
+  int (*batch_blocks_per_sm)(int collision, int threads);
 };
 
 const Ops* ops_d2q9_f64();

@@ -38,6 +38,13 @@ int ctx_bind(lbm_ctx* c, void* a, void* b, const uint8_t* mask, void* scratch);
 void ctx_set_state(lbm_ctx* c, int cur, long long t);
 void ctx_get_state(const lbm_ctx* c, int* cur, long long* t);
 void ctx_mark_view(lbm_ctx* c);
+void ctx_set_flag(lbm_ctx* c, unsigned int* flag);
+cudaStream_t ctx_stream(const lbm_ctx* c);
+const Ops* ctx_ops(const lbm_ctx* c);
+const std::vector<Variant>& ctx_variants(const lbm_ctx* c);
+int ctx_variant(const lbm_ctx* c);
+StepLaunch ctx_step_launch(lbm_ctx* c, const Variant& v);
+void ctx_delete(lbm_ctx* c);
 void ctx_add_launches(lbm_ctx* c, long long n);
 int ctx_fail(int code, const char* what);
 int reset_flag(lbm_ctx* c);

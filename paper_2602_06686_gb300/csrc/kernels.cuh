@@ -57,7 +57,7 @@ __device__ __forceinline__ R shfl_down1(R v) {
 
 // Pre-collision populations of the NV nodes [x0, x0 + NV) of row (y, z).
 // Must be called by all 32 lanes of a warp (shuffles); `active` lanes load.
-template <class L, class S, int NV, bool MASK>
+template <class L, class S, int NV, bool MASK, int LD = LD_NC>
 __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __restrict__ src,
                                        const uint8_t* __restrict__ mask, int x0, int y, int z,
                                        int lane, bool active, typename S::R (&f)[L::Q][NV]) {
@@ -79,14 +79,14 @@ __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __rest
       else wall = true;
     }
     if (wall) {  // uniform across the warp: whole row bounces
-      if (active) ld_dec<S, NV>(opp_own + x0, f[i]);
+      if (active) ld_dec<S, NV, LD>(opp_own + x0, f[i]);
       continue;
     }
     const long long srow = ((long long)zs * G.ny + ys) * G.pitch;
     const T* row = src + i * G.plane + srow;
     R v[NV];
     if (active) {
-      ld_dec<S, NV>(row + x0, v);
+      ld_dec<S, NV, LD>(row + x0, v);
     } else {
 #pragma unroll
       for (int k = 0; k < NV; ++k) v[k] = R(0);
@@ -102,9 +102,9 @@ __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __rest
         f[i][0] = left;
       } else if (active) {
         const int xs = x0 - 1;
-        if (xs >= 0) f[i][0] = S::dec(row[xs]);
-        else if (G.per[0]) f[i][0] = S::dec(row[G.nx - 1]);
-        else f[i][0] = S::dec(opp_own[x0]);
+        if (xs >= 0) f[i][0] = ld1<S, LD>(row + xs);
+        else if (G.per[0]) f[i][0] = ld1<S, LD>(row + G.nx - 1);
+        else f[i][0] = ld1<S, LD>(opp_own + x0);
       }
     } else {  // ex == -1: source x + 1
       const R right = shfl_down1(v[0]);
@@ -112,9 +112,9 @@ __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __rest
       for (int k = 0; k < NV - 1; ++k) f[i][k] = v[k + 1];
       const int xs = x0 + NV;
       if (active) {
-        if (xs < G.nx) f[i][NV - 1] = lane < 31 ? right : S::dec(row[xs]);
-        else if (G.per[0]) f[i][NV - 1] = S::dec(row[0]);
-        else f[i][NV - 1] = S::dec(opp_own[x0 + NV - 1]);
+        if (xs < G.nx) f[i][NV - 1] = lane < 31 ? right : ld1<S, LD>(row + xs);
+        else if (G.per[0]) f[i][NV - 1] = ld1<S, LD>(row);
+        else f[i][NV - 1] = ld1<S, LD>(opp_own + x0 + NV - 1);
       }
     }
     if constexpr (MASK) {
@@ -128,7 +128,7 @@ __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __rest
             if (!G.per[0]) continue;  // already bounced at the x wall
             xs = xs < 0 ? xs + G.nx : xs - G.nx;
           }
-          if (mrow[xs]) f[i][k] = S::dec(opp_own[x0 + k]);
+          if (mrow[xs]) f[i][k] = ld1<S, LD>(opp_own + x0 + k);
         }
       }
     }
@@ -136,7 +136,7 @@ __device__ __forceinline__ void gather(const Geo& G, const typename S::T* __rest
 }
 
 // One fused update of a tile of rows: gather, collide, store.
-template <class L, int COLL, class S, int NV, bool MASK>
+template <class L, int COLL, class S, int NV, bool MASK, int LD = LD_NC>
 __device__ __forceinline__ void update_chunk(const StepArgs<typename S::R>& a, int x0, int y, int z,
                                              int lane) {
   using T = typename S::T;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void update_chunk(const StepArgs<typename S::R>& a, i
   const T* __restrict__ src = static_cast<const T*>(a.src);
   T* __restrict__ dst = static_cast<T*>(a.dst);
   R f[L::Q][NV];
-  gather<L, S, NV, MASK>(G, src, a.mask, x0, y, z, lane, active, f);
+  gather<L, S, NV, MASK, LD>(G, src, a.mask, x0, y, z, lane, active, f);
   if (!active) return;
   bool anybad = false;
   bool solid[NV];

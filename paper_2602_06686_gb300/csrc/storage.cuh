@@ -70,26 +70,55 @@ struct RawT<16> {
   using type = uint4;
 };
 
-__device__ __forceinline__ unsigned char ldg_raw(const unsigned char* p) { return __ldg(p); }
-__device__ __forceinline__ unsigned short ldg_raw(const unsigned short* p) { return __ldg(p); }
-__device__ __forceinline__ unsigned int ldg_raw(const unsigned int* p) { return __ldg(p); }
-__device__ __forceinline__ uint2 ldg_raw(const uint2* p) { return __ldg(p); }
-__device__ __forceinline__ uint4 ldg_raw(const uint4* p) { return __ldg(p); }
+// Load policies: LD_NC reads through the non-coherent (texture / L1) path, valid
+// when the buffer was written by an earlier kernel launch; LD_CG caches in L2
+// only, required when another SM of the SAME launch wrote the data (the
+// persistent batched kernel), since L1 is not coherent across SMs.
+enum { LD_NC = 0, LD_CG = 1 };
+
+template <int LD>
+__device__ __forceinline__ unsigned char ld_raw(const unsigned char* p) {
+  return LD == LD_CG ? __ldcg(p) : __ldg(p);
+}
+template <int LD>
+__device__ __forceinline__ unsigned short ld_raw(const unsigned short* p) {
+  return LD == LD_CG ? __ldcg(p) : __ldg(p);
+}
+template <int LD>
+__device__ __forceinline__ unsigned int ld_raw(const unsigned int* p) {
+  return LD == LD_CG ? __ldcg(p) : __ldg(p);
+}
+template <int LD>
+__device__ __forceinline__ uint2 ld_raw(const uint2* p) {
+  return LD == LD_CG ? __ldcg(p) : __ldg(p);
+}
+template <int LD>
+__device__ __forceinline__ uint4 ld_raw(const uint4* p) {
+  return LD == LD_CG ? __ldcg(p) : __ldg(p);
+}
 
 // NV consecutive elements starting at p (p aligned to NV * sizeof(T)).
-template <typename T, int NV>
+template <typename T, int NV, int LD = LD_NC>
 __device__ __forceinline__ void ld_vec(const T* p, T (&out)[NV]) {
   using Raw = typename RawT<sizeof(T) * NV>::type;
-  Raw r = ldg_raw(reinterpret_cast<const Raw*>(p));
+  Raw r = ld_raw<LD>(reinterpret_cast<const Raw*>(p));
   memcpy(out, &r, sizeof(Raw));
 }
 
-template <class S, int NV>
+template <class S, int NV, int LD = LD_NC>
 __device__ __forceinline__ void ld_dec(const typename S::T* p, typename S::R (&out)[NV]) {
   typename S::T t[NV];
-  ld_vec<typename S::T, NV>(p, t);
+  ld_vec<typename S::T, NV, LD>(p, t);
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = S::dec(t[k]);
+}
+
+// One element.
+template <class S, int LD = LD_NC>
+__device__ __forceinline__ typename S::R ld1(const typename S::T* p) {
+  typename S::T t[1];
+  ld_vec<typename S::T, 1, LD>(p, t);
+  return S::dec(t[0]);
 }
 
 template <class S, int NV>

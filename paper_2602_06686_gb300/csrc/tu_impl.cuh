@@ -4,6 +4,7 @@
 #include "dispatch.h"
 #include "kernels.cuh"
 #include "aa.cuh"
+#include "batch.cuh"
 
 namespace lbm {
 
@@ -231,6 +232,48 @@ struct TU {
     return cudaGetLastError();
   }
 
+  template <int COLL>
+  static void* batch_fn() {
+    return reinterpret_cast<void*>(&k_batch<L, COLL, S>);
+  }
+  static void* batch_kernel(int coll) {
+    switch (coll) {
+      case C_TRT:
+        return batch_fn<C_TRT>();
+      case C_TRT_RLB:
+        return batch_fn<C_TRT_RLB>();
+      case C_P_TRT:
+        return batch_fn<C_P_TRT>();
+    }
+    return nullptr;
+  }
+  static int batch_blocks_per_sm(int coll, int threads) {
+    void* fn = batch_kernel(coll);
+    int n = 0;
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess)
+      return 0;
+    return n;
+  }
+  static cudaError_t batch(const BatchLaunch& b) {
+    void* fn = batch_kernel(b.collision);
+    if (!fn) return cudaErrorInvalidValue;
+    BarrierWords* bar = static_cast<BarrierWords*>(b.bar);
+    void* args[] = {(void*)&b.desc,  (void*)&b.tiles,    (void*)&b.ntiles, (void*)&b.A,
+                    (void*)&b.B,     (void*)&b.nsteps,   (void*)&b.parity0, (void*)&b.step0,
+                    (void*)&b.flags, (void*)&bar,        (void*)&b.expected, (void*)&b.timeout_ns};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.blocks);
+    cfg.blockDim = dim3(b.bx, b.by);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
+
   static const Ops* ops() {
     static Ops o = [] {
       Ops r{};
@@ -246,6 +289,8 @@ struct TU {
       r.set_pop = &set_pop;
       r.get_pop = &get_pop;
       r.macros = &macros;
+      r.batch = &batch;
+      r.batch_blocks_per_sm = &batch_blocks_per_sm;
       return r;
     }();
     return &o;

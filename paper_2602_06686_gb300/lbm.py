@@ -207,6 +207,8 @@ class Lattice:
     # -- state
     def _dev64(self, a, shape):
         import torch
+        if isinstance(a, np.ndarray) and not a.flags.writeable:
+            a = a.copy()
         t = torch.as_tensor(a, dtype=torch.float64)
         return t.to(self.pop_a.device).reshape(shape).contiguous()
 
@@ -343,6 +345,114 @@ class Lattice:
         if getattr(self, "ctx", None) and self.ctx.value:
             self.lib.lbm_destroy(self.ctx)
             self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _View(Lattice):
+    """Lattice i of a Batch: shares the batch's arenas and scratch."""
+
+    def __init__(self, batch, i, ctx, params):
+        self.lib = batch.lib
+        self.p = params
+        self.Q = Q_OF[params.lattice]
+        self.D = D_OF[params.lattice]
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+        self.stream = batch.stream
+        self.pop_a = batch.pop_a  # for the device of temporaries
+        self.ctx = ctx
+        self._batch = batch
+
+    def step(self, n: int = 1):
+        raise RuntimeError("lattices of a batch advance together: use Batch.step")
+
+    def close(self):
+        self.ctx = ctypes.c_void_p()
+
+
+class Batch:
+    """Many independent lattices advanced by one persistent kernel."""
+
+    def __init__(self, params: list, stream=None):
+        import torch
+        self.lib = load_library()
+        self.n = len(params)
+        arr = (Params * self.n)()
+        for i, kw in enumerate(params):
+            arr[i] = make_params(**kw)
+        self.params = arr
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self.lib.lbm_batch_buffer_sizes(self.n, arr, ctypes.byref(a), ctypes.byref(b)),
+               "lbm_batch_buffer_sizes")
+        self.pop_bytes, self.scratch_bytes = a.value, b.value
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.pop_a = torch.empty(self.pop_bytes, dtype=torch.uint8, device=dev)
+        self.pop_b = torch.empty(self.pop_bytes, dtype=torch.uint8, device=dev)
+        self.scratch = torch.empty(self.scratch_bytes, dtype=torch.uint8, device=dev)
+        self.h = ctypes.c_void_p()
+        _check(self.lib.lbm_batch_create(self.n, arr, _stream_handle(self.stream),
+                                         ctypes.byref(self.h)), "lbm_batch_create")
+        _check(self.lib.lbm_batch_bind(self.h, _dev_ptr(self.pop_a), _dev_ptr(self.pop_b),
+                                       _dev_ptr(self.scratch)), "lbm_batch_bind")
+        self.views = []
+        for i in range(self.n):
+            v = ctypes.c_void_p()
+            _check(self.lib.lbm_batch_lattice(self.h, i, ctypes.byref(v)), "lbm_batch_lattice")
+            self.views.append(_View(self, i, v, arr[i]))
+
+    @property
+    def nodes(self) -> int:
+        return sum(v.N for v in self.views)
+
+    def lattice(self, i: int) -> Lattice:
+        return self.views[i]
+
+    def step(self, n: int, mode: int = 0):
+        _check(self.lib.lbm_batch_step(self.h, int(n), int(mode)), "lbm_batch_step")
+
+    def variants(self):
+        n = ctypes.c_int()
+        _check(self.lib.lbm_batch_variant_count(self.h, ctypes.byref(n)), "variant count")
+        buf = ctypes.create_string_buffer(64)
+        out = []
+        for v in range(n.value):
+            _check(self.lib.lbm_batch_variant_name(self.h, v, buf, 64), "variant name")
+            out.append(buf.value.decode())
+        return out
+
+    def set_variant(self, v: int):
+        _check(self.lib.lbm_batch_set_variant(self.h, int(v)), "lbm_batch_set_variant")
+
+    def autotune(self, steps: int = 4):
+        n = len(self.variants())
+        times = (ctypes.c_float * n)()
+        chosen = ctypes.c_int()
+        _check(self.lib.lbm_batch_autotune(self.h, int(steps), ctypes.byref(chosen), times),
+               "lbm_batch_autotune")
+        return chosen.value, list(times)
+
+    def set_barrier(self, timeout_s: float, extra: int = 0):
+        _check(self.lib.lbm_batch_set_barrier(self.h, float(timeout_s), int(extra)),
+               "lbm_batch_set_barrier")
+
+    @property
+    def launches(self) -> int:
+        v = ctypes.c_longlong()
+        _check(self.lib.lbm_batch_launches(self.h, ctypes.byref(v)), "lbm_batch_launches")
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            for v in self.views:
+                v.close()
+            self.lib.lbm_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
 
     def __del__(self):
         try:
