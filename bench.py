@@ -347,6 +347,8 @@ def run_ours(args):
     g.init_equilibrium(rho, u)
     chosen, times = g.autotune(reps=3)
     variant = g.variants()[chosen]
+    names = g.variants()
+    tune = dict(sorted(((names[v], round(t, 4)) for v, t in enumerate(times)), key=lambda kv: kv[1])[:8])
     N = g.N
     st = g.stream
 
@@ -440,7 +442,8 @@ def run_ours(args):
                                f"Re=1e5, 1/tau-=1.6, A/B buffers",
                    "updates_per_step": inner, "diagnostics_per_step": 1,
                    "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
-                   "variant": variant, "parallelism": f"replicas x{world}"},
+                   "variant": variant, "autotune_ms": tune,
+                   "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profile_traffic(khash),
                      "peak_source": peaks["source"], "bytes_per_node": bpn,

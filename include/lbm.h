@@ -195,6 +195,13 @@ int lbm_restore(lbm_ctx* ctx, const void* src, size_t bytes, long long t);
 /* Number of kernels this context has enqueued since creation (all entry points). */
 int lbm_launch_count(const lbm_ctx* ctx, long long* launches);
 
+/* Limit, in seconds (0 < limit <= 60, default 2), of every bounded wait of the
+ * pipelined kernel variant (its shared-memory stage barriers).  For tests:
+ * test_extra_bytes > 0 makes every stage wait for that many bytes that never
+ * arrive, so each wait runs out, the kernel returns, and lbm_status reports
+ * LBM_ERR_TIMEOUT; pass 0 to run normally. */
+int lbm_set_wait_limit(lbm_ctx* ctx, double seconds, int test_extra_bytes);
+
 /* Text of the most recent error raised in the calling thread (CUDA error name
  * and the call that failed), or "" if none. */
 const char* lbm_last_error(void);

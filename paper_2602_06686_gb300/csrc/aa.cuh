@@ -68,8 +68,7 @@ __device__ __forceinline__ void aa_node(const StepArgs<typename S::R>& a, int x,
     slot[i] = aa_state_slot<L>(G, mask, parity, x, y, z, i);
     g[i] = S::dec(buf[slot[i]]);
   }
-  bool bad;
-  collide<L, COLL, R>(g, a.c, bad);
+  const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
   if (parity == 0) {
     const long long own = ((long long)z * G.ny + y) * G.pitch + x;
 #pragma unroll
@@ -78,7 +77,7 @@ __device__ __forceinline__ void aa_node(const StepArgs<typename S::R>& a, int x,
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) buf[aa_odd_dst<L>(G, mask, x, y, z, i)] = S::enc(g[i]);
   }
-  if (bad) atomicMin(a.flag, a.step);
+  record_bad(a.flag, a.step, bad);
 }
 
 template <class L, int COLL, class S, int NV, bool MASK>

@@ -215,6 +215,7 @@ int run_sequential(lbm_batch* b, int n) {
       ctx_set_state(v, b->cur, b->t);
       const std::vector<Variant>& vs = ctx_variants(v);
       StepLaunch sl = ctx_step_launch(v, vs[ctx_variant(v)]);
+      sl.flag = reinterpret_cast<unsigned int*>(b->scratch + kBatchFlags) + i;
       cudaError_t e = b->ops->step(sl);
       ++launches;
       if (e != cudaSuccess) return cuda_fail(e, "sequential step launch");
@@ -290,11 +291,8 @@ int lbm_batch_bind(lbm_batch* b, void* pop_a, void* pop_b, void* scratch) {
   for (int i = 0; i < b->bp.n; ++i) {
     const Plan& p = b->bp.pl[i];
     desc[i].g = p.g;
-    desc[i].rho0 = p.p.rho0;
-    desc[i].cp = p.cp;
-    desc[i].cm = p.cm;
-    desc[i].hg = p.hg;
-    for (int k = 0; k < 3; ++k) desc[i].F[k] = p.p.force[k];
+    desc[i].cd = p.coef;
+    desc[i].cf = coef_cast<float>(p.coef);
     desc[i].off = (long long)b->bp.off[i];
     ctx_bind(b->views[i], b->A + b->bp.off[i], b->B + b->bp.off[i], nullptr, b->scratch + b->bp.view_off);
     ctx_set_flag(b->views[i], reinterpret_cast<unsigned int*>(b->scratch + kBatchFlags) + i);

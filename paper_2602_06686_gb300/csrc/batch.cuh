@@ -84,14 +84,12 @@ __global__ void __launch_bounds__(256)
       a.g.nz = d.g.nz;
       a.g.pitch = d.g.pitch;
       a.g.plane = d.g.plane;
-      for (int k = 0; k < 3; ++k) {
-        a.g.per[k] = d.g.per[k];
-        a.c.F[k] = R(d.F[k]);
+      for (int k = 0; k < 3; ++k) a.g.per[k] = d.g.per[k];
+      if constexpr (sizeof(R) == sizeof(double)) {
+        a.c = d.cd;
+      } else {
+        a.c = d.cf;
       }
-      a.c.rho0 = R(d.rho0);
-      a.c.cp = R(d.cp);
-      a.c.cm = R(d.cm);
-      a.c.hg = R(d.hg);
       a.src = src + d.off;
       a.dst = dst + d.off;
       a.mask = nullptr;

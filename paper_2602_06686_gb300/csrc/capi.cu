@@ -110,30 +110,49 @@ int plan(const lbm_params* p, Plan* out) {
   r.cp = 1.0 - wp;
   r.cm = 1.0 - wmk;
   r.hg = 1.0 - 0.5 * wp;
+  r.force = p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0;
+  if (p->lattice == LBM_D2Q9)
+    fill_coef<D2Q9>(p->rho0, wp, wmk, r.kernel_collision, p->force, &r.coef);
+  else
+    fill_coef<D3Q19>(p->rho0, wp, wmk, r.kernel_collision, p->force, &r.coef);
   *out = r;
   return LBM_OK;
 }
 
-std::vector<Variant> variants_for(const Plan& pl, const Ops* ops) {
+std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked) {
   static const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
   std::vector<Variant> v;
+  // pipelined bulk-copy kernel: A/B layout, no solid mask, rows a multiple of 16 bytes
+  const int H = 16 / pl.esize;
+  if (pl.p.layout == LBM_LAYOUT_AB && !masked && pl.p.nx % H == 0 && pl.p.nx >= 2 * H) {
+    static const int tiles[] = {256, 512, 128};
+    static const int depths[] = {4, 6, 3, 8};
+    for (int X : tiles)
+      for (int st : depths) {
+        const size_t smem = ops->tma_smem(X, st);
+        if (smem > 0 && smem <= 110 * 1024) v.push_back(Variant{1, 0, 0, 0, X, st});
+      }
+  }
   for (int k = 0; k < ops->n_nv; ++k) {
     const int nv = ops->nvs[k];
     if (pl.p.nx % nv != 0) continue;
     if (pl.p.layout == LBM_LAYOUT_AA && nv != 1) continue;
     for (auto& s : shapes)
-      if ((pl.p.ny + s[1] - 1) / s[1] <= 65535) v.push_back(Variant{nv, s[0], s[1]});
+      if ((pl.p.ny + s[1] - 1) / s[1] <= 65535) v.push_back(Variant{0, nv, s[0], s[1], 0, 0});
   }
   return v;
 }
 
 int default_variant(const Plan& pl, const std::vector<Variant>& vs) {
-  // widest vector that keeps the registers of one thread moderate, 256 threads
+  // the pipelined kernel when available, else the widest vector that keeps the
+  // registers of one thread moderate, 256 threads
+  for (size_t k = 0; k < vs.size(); ++k)
+    if (vs[k].kind == 1) return (int)k;
   const int budget = pl.Q == 9 ? 16 : 8;  // bytes per plane per thread
   int best = 0, best_nv = 0;
   for (size_t k = 0; k < vs.size(); ++k) {
     const Variant& v = vs[k];
-    if (v.nv * pl.esize > budget || v.bx * v.by != 256) continue;
+    if (v.kind != 0 || v.nv * pl.esize > budget || v.bx * v.by != 256) continue;
     if (v.nv > best_nv || (v.nv == best_nv && v.bx == 64)) {
       best = (int)k;
       best_nv = v.nv;
@@ -160,6 +179,9 @@ struct lbm_ctx {
   long long launches = 0;
   std::vector<Variant> vars;
   int var = 0;
+  int sms = 0;
+  long long wait_ns = 2000000000LL;
+  int extra_tx = 0;
 };
 
 namespace lbm {
@@ -183,11 +205,12 @@ StepLaunch step_of(lbm_ctx* c, const Variant& v) {
   StepLaunch s{};
   s.g = c->pl.g;
   s.collision = c->pl.kernel_collision;
-  s.rho0 = c->pl.p.rho0;
-  s.cp = c->pl.cp;
-  s.cm = c->pl.cm;
-  s.hg = c->pl.hg;
-  for (int k = 0; k < 3; ++k) s.F[k] = c->pl.p.force[k];
+  s.force = c->pl.force;
+  s.c = c->pl.coef;
+  s.err = reinterpret_cast<int*>(c->scratch + kErrOffset);
+  s.wait_ns = c->wait_ns;
+  s.extra_tx = c->extra_tx;
+  s.sms = c->sms;
   s.mask = c->mask;
   s.flag = flag_ptr(c);
   s.step = (unsigned int)(c->t < 0xfffffffeLL ? c->t : 0xfffffffeLL);
@@ -212,7 +235,8 @@ int ctx_new(const Plan& pl, cudaStream_t st, lbm_ctx** out) {
   c->ops = pick_ops(pl.p.lattice, pl.p.storage);
   c->stream = st;
   cudaGetDevice(&c->device);
-  c->vars = variants_for(pl, c->ops);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->vars = variants_for(pl, c->ops, false);
   c->var = default_variant(pl, c->vars);
   *out = c;
   return LBM_OK;
@@ -227,10 +251,15 @@ int ctx_bind(lbm_ctx* c, void* a, void* b, const uint8_t* mask, void* scratch) {
   c->bound = true;
   c->cur = 0;
   c->t = 0;
+  c->vars = variants_for(c->pl, c->ops, mask != nullptr);
+  c->var = default_variant(c->pl, c->vars);
   return LBM_OK;
 }
 
 int reset_flag(lbm_ctx* c) {
+  int rc = cuda_check(cudaMemsetAsync(c->scratch + kErrOffset, 0, sizeof(int), c->stream),
+                      "reset error word");
+  if (rc) return rc;
   return cuda_check(cudaMemsetAsync(flag_ptr(c), 0xff, sizeof(unsigned int), c->stream),
                     "reset divergence flag");
 }
@@ -465,12 +494,18 @@ int lbm_velocity_l2(lbm_ctx* c, const double* u_ref, double* out) {
 int lbm_status(lbm_ctx* c, long long* first_step) {
   CHECK_CTX(c);
   unsigned int v = 0;
+  int err = 0;
   int rc = cuda_check(cudaMemcpyAsync(&v, flag_ptr(c), sizeof(v), cudaMemcpyDeviceToHost, c->stream),
                       "read divergence flag");
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(&err, c->scratch + kErrOffset, sizeof(err), cudaMemcpyDeviceToHost,
+                                  c->stream),
+                  "read error word");
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
   if (rc) return rc;
   if (first_step) *first_step = v == 0xffffffffu ? -1 : (long long)v;
+  if (err) return fail(LBM_ERR_TIMEOUT, "a bounded device wait ran out");
   return v == 0xffffffffu ? LBM_OK : LBM_ERR_DIVERGED;
 }
 
@@ -499,6 +534,14 @@ int lbm_restore(lbm_ctx* c, const void* src, size_t bytes, long long t) {
                     "restore");
 }
 
+int lbm_set_wait_limit(lbm_ctx* c, double seconds, int test_extra_bytes) {
+  if (!c || !(seconds > 0.0) || seconds > 60.0 || test_extra_bytes < 0 || test_extra_bytes > (1 << 16))
+    return fail(LBM_ERR_ARG, "limit in (0, 60] s, extra bytes in [0, 65536]");
+  c->wait_ns = (long long)(seconds * 1e9);
+  c->extra_tx = test_extra_bytes;
+  return LBM_OK;
+}
+
 int lbm_launch_count(const lbm_ctx* c, long long* launches) {
   if (!c || !launches) return fail(LBM_ERR_ARG, "NULL argument");
   *launches = c->launches;
@@ -514,7 +557,10 @@ int lbm_variant_count(const lbm_ctx* c, int* n) {
 int lbm_variant_name(const lbm_ctx* c, int v, char* buf, size_t len) {
   if (!c || !buf || v < 0 || v >= (int)c->vars.size()) return fail(LBM_ERR_ARG, "bad variant");
   const Variant& x = c->vars[v];
-  snprintf(buf, len, "nv%d_b%dx%d", x.nv, x.bx, x.by);
+  if (x.kind == 1)
+    snprintf(buf, len, "tma_X%d_s%d", x.X, x.stages);
+  else
+    snprintf(buf, len, "nv%d_b%dx%d", x.nv, x.bx, x.by);
   return LBM_OK;
 }
 

@@ -1,0 +1,515 @@
+// collide_v.cuh -- the per-node collision operators, generic over the
+// arithmetic type V: float, double, or F2 (two FP32 nodes advanced together
+// with the packed f32x2 instructions of sm_100+).
+//
+// Input and output are the shifted populations g_i = f_i - w_i rho0.  The
+// operators (arXiv 2602.06686):
+//   f* = f_eq + (1 - w+) R2 + (1 - w-) R3 + F_i/2 + (1 - w+/2) S+
+//   TRT      R2 = fneq+                        R3 = fneq- + F_i/2
+//   P-TRT    R2 = fneq+ - P_G fneq (Eq. PTRT)  R3 = fneq- + F_i/2 (Eq. R3_force)
+//   TRT-RLB  R2 = P^(2) fneq, R3 = P^(3) fneq  (Eq. R2R3_hermite as w-orthogonal projections)
+// with rho and the half-force velocity u of Eq. macro, the third-order
+// equilibrium of Eq. feq, written per inversion pair (i, ibar) as
+//   f_eq,i +- f_eq,ibar = 2 w [drho + rho (4.5 eu^2 - 1.5 u^2)]  +-  2 w rho eu (3 + 4.5 (eu^2 - u^2))
+// (H3_i : uuu = (e_i.u)^3 - 3 cs^2 u^2 (e_i.u) on any velocity set),
+// F_i = 3 w e_i.F and S+ = w (9 eu eF - 3 u.F).  The force reading keeps the
+// first-order term of Sec. 2.2 and the whole Guo source at (1 - w+/2), which
+// makes the antisymmetric force content F_i/2 + (1-w-) R3 for every rate.
+//
+// Ghost modes (hand-derived, w-orthogonal, integer values G(k, i)):
+//   D2Q9 : phi = (ex^2 - cs^2)(ey^2 - cs^2) = cs^4 G with G = 1 (rest), -2
+//          (axial), 4 (diagonal) and norm 4 cs^8 (App. A.1, Eq. R2_D2Q9).
+//   D3Q19: the printed products (e_a^2 - cs^2)(e_b^2 - cs^2) are neither mutually
+//          orthogonal nor orthogonal to H2 on D3Q19; the ghost subspace (the
+//          complement of span{1, H2} in the symmetric subspace, Eq. S_decomp) is
+//          spanned by phi~_ab = (e_a^2 - cs^2)(e_b^2 - cs^2) + (cs^2/2)(e_c^2 - cs^2)
+//          and diagonalised into g_e = phi~_xy + phi~_yz + phi~_zx (norm 9/2 cs^8),
+//          g_1 = phi~_xy - phi~_yz (9 cs^8), g_2 = phi~_xy + phi~_yz - 2 phi~_zx
+//          (27 cs^8) with values
+//              g_e*6: rest 1, axial -2, diagonal 1
+//              g_1*2: x pair -1, z pair 1, xy diagonals 1, yz diagonals -1
+//              g_2*2: x pair 1, y pair -2, z pair 1, xy 1, yz 1, xz -2.
+//   P_G fneq = sum_k w_i G(k,i) (s_k^2 / N_k) sum_j G(k,j) fneq_j.
+// TRT-RLB on D3Q19: the third-order components m_ab = e_a (e_b^2 - cs^2) of the
+// same odd axis a overlap (<m_ab, m_ac>_w = -cs^6); their sum (norm 2 cs^6) and
+// difference (norm 6 cs^6) are w-orthogonal.
+//
+// Every operation is an explicitly rounded add / sub / mul / fma, so the scalar
+// and packed paths give bit-identical results and the compiler cannot regroup.
+#pragma once
+#include <string.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+enum { C_TRT = 0, C_TRT_RLB = 1, C_P_TRT = 2 };
+
+struct alignas(8) F2 {
+  float x, y;
+};
+
+template <typename V>
+struct Ar;
+
+#if defined(__CUDA_ARCH__)
+template <>
+struct Ar<float> {
+  using S = float;
+  __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ __forceinline__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
+  __device__ __forceinline__ static float c(double v) { return float(v); }
+  __device__ __forceinline__ static float c(float v) { return v; }
+  __device__ __forceinline__ static unsigned bad(float rho, float usq) {
+    return (!(rho > 0.f) || !(usq <= 1.f)) ? 1u : 0u;
+  }
+};
+template <>
+struct Ar<double> {
+  using S = double;
+  __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
+  __device__ __forceinline__ static double c(double v) { return v; }
+  __device__ __forceinline__ static unsigned bad(double rho, double usq) {
+    return (!(rho > 0.0) || !(usq <= 1.0)) ? 1u : 0u;
+  }
+};
+template <>
+struct Ar<F2> {
+  using S = float;
+  __device__ __forceinline__ static unsigned long long u(F2 a) {
+    unsigned long long r;
+    memcpy(&r, &a, 8);
+    return r;
+  }
+  __device__ __forceinline__ static F2 f(unsigned long long a) {
+    F2 r;
+    memcpy(&r, &a, 8);
+    return r;
+  }
+  __device__ __forceinline__ static F2 add(F2 a, F2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
+    return f(r);
+  }
+  __device__ __forceinline__ static F2 sub(F2 a, F2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
+    return f(r);
+  }
+  __device__ __forceinline__ static F2 mul(F2 a, F2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
+    return f(r);
+  }
+  __device__ __forceinline__ static F2 fma(F2 a, F2 b, F2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(u(a)), "l"(u(b)), "l"(u(c)));
+    return f(r);
+  }
+  __device__ __forceinline__ static F2 rcp(F2 a) { return F2{__frcp_rn(a.x), __frcp_rn(a.y)}; }
+  __device__ __forceinline__ static F2 c(double v) { return F2{float(v), float(v)}; }
+  __device__ __forceinline__ static F2 c(float v) { return F2{v, v}; }
+  __device__ __forceinline__ static unsigned bad(F2 rho, F2 usq) {
+    return Ar<float>::bad(rho.x, usq.x) | (Ar<float>::bad(rho.y, usq.y) << 1);
+  }
+};
+#else
+// Host compilation (used only to check the arithmetic against the oracle on a CPU).
+template <typename T>
+struct ArHost {
+  using S = T;
+  static T add(T a, T b) { return a + b; }
+  static T sub(T a, T b) { return a - b; }
+  static T mul(T a, T b) { return a * b; }
+  static T fma(T a, T b, T c) { return __builtin_fma(a, b, c); }
+  static T rcp(T a) { return T(1) / a; }
+  static T c(double v) { return T(v); }
+  static T c(float v) { return T(v); }
+  static unsigned bad(T rho, T usq) { return (!(rho > 0) || !(usq <= 1)) ? 1u : 0u; }
+};
+template <>
+struct Ar<double> : ArHost<double> {};
+template <>
+struct Ar<float> : ArHost<float> {
+  static float fma(float a, float b, float c) { return __builtin_fmaf(a, b, c); }
+};
+#endif
+
+// Per-launch constants (computed on the host in FP64, stored in the arithmetic
+// precision).  The force terms are compiled out when the force is zero
+// (FORCE = false).  Per-direction entries are used at pair representatives.
+constexpr int kQMax = 19;
+template <typename S>
+struct CoefV {
+  S rho0;
+  S cp;            // 1 - w+
+  S cm;            // 1 - w-  (as run: BGK w- = w+, RLB w- = 1)
+  S Fh[3];         // F / 2 (half-force velocity, Eq. macro)
+  S F[3];          // F (for u.F)
+  S fe[kQMax];     // 9 w_i (e_i.F) (1 - w+/2): coefficient of e_i.u in S+_i
+  S fu[kQMax];     // -3 w_i (1 - w+/2): coefficient of u.F in S+_i
+  S fa[kQMax];     // antisymmetric force content: F_i/2 (2 - w-) (TRT, P-TRT) or F_i/2 (TRT-RLB)
+};
+
+// ---- ghost tables (integer values and s_k^2 / N_k) ------------------------
+template <class L>
+struct GhostT;
+
+template <>
+struct GhostT<D2Q9> {
+  static constexpr int NG = 1;
+  __host__ __device__ static constexpr int G(int, int i) { return i == 0 ? 1 : (i <= 4 ? -2 : 4); }
+  // phi = G/9, N = 4/81 -> s^2/N = 1/4
+  __host__ __device__ static constexpr double coef(int) { return 0.25; }
+};
+
+template <>
+struct GhostT<D3Q19> {
+  static constexpr int NG = 3;
+  // class: 0 rest, 1/2/3 axial along x/y/z, 4 xy, 5 xz, 6 yz diagonal
+  __host__ __device__ static constexpr int cls(int i) {
+    return i == 0 ? 0 : (i <= 6 ? 1 + (i - 1) / 2 : 4 + (i - 7) / 4);
+  }
+  __host__ __device__ static constexpr int G(int k, int i) {
+    constexpr int ge[7] = {1, -2, -2, -2, 1, 1, 1};
+    constexpr int g1[7] = {0, -1, 0, 1, 1, 0, -1};
+    constexpr int g2[7] = {0, 1, -2, 1, 1, -2, 1};
+    return k == 0 ? ge[cls(i)] : (k == 1 ? g1[cls(i)] : g2[cls(i)]);
+  }
+  // g_e = G/6, N = 1/18 -> 1/2;  g_1 = G/2, N = 1/9 -> 9/4;  g_2 = G/2, N = 1/3 -> 3/4
+  __host__ __device__ static constexpr double coef(int k) { return k == 0 ? 0.5 : (k == 1 ? 2.25 : 0.75); }
+};
+
+template <class L>
+__host__ __device__ constexpr int ecomp(int i, int a) {
+  return a == 0 ? L::cx(i) : (a == 1 ? L::cy(i) : L::cz(i));
+}
+
+// sum_a e_i,a v_a: the positive components are added first, then the negative
+// ones subtracted (every pair representative has a +1 component).
+template <class L, typename V>
+__device__ __forceinline__ V edot(int i, const V (&v)[3]) {
+  using A = Ar<V>;
+  V acc = A::c(0.0);
+  bool init = false;
+#pragma unroll
+  for (int a = 0; a < L::D; ++a)
+    if (ecomp<L>(i, a) == 1) {
+      acc = init ? A::add(acc, v[a]) : v[a];
+      init = true;
+    }
+#pragma unroll
+  for (int a = 0; a < L::D; ++a)
+    if (ecomp<L>(i, a) == -1) acc = A::sub(acc, v[a]);
+  return acc;
+}
+
+// The collision.  Returns a bit mask of the lanes (nodes) that are not finite,
+// have rho <= 0 or |u| > 1.
+template <class L, int COLL, bool FORCE, typename V>
+__device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename Ar<V>::S>& c) {
+  using A = Ar<V>;
+  constexpr int Q = L::Q;
+  // ---- pair sums / differences, density and momentum
+  V s[Q], d[Q];
+  V drho = g[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!is_pair_rep<L>(i)) continue;
+    s[i] = A::add(g[i], g[L::opp(i)]);
+    d[i] = A::sub(g[i], g[L::opp(i)]);
+    drho = A::add(drho, s[i]);
+  }
+  V j[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    j[a] = A::c(0.0);
+    if (a >= L::D) continue;
+    bool init = false;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      const int e = ecomp<L>(i, a);
+      if (e == 1) {
+        j[a] = init ? A::add(j[a], d[i]) : d[i];
+        init = true;
+      }
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      if (ecomp<L>(i, a) == -1) j[a] = A::sub(j[a], d[i]);
+    }
+  }
+  const V rho = A::add(A::c(c.rho0), drho);
+  const V inv = A::rcp(rho);
+  V u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= L::D) {
+      u[a] = A::c(0.0);
+      continue;
+    }
+    u[a] = FORCE ? A::mul(A::add(j[a], A::c(c.Fh[a])), inv) : A::mul(j[a], inv);
+  }
+  V usq = A::mul(u[0], u[0]);
+  usq = A::fma(u[1], u[1], usq);
+  if (L::D == 3) usq = A::fma(u[2], u[2], usq);
+  const unsigned badmask = A::bad(rho, usq);
+
+  // per-node scalars
+  const V rho36 = A::mul(rho, A::c(1.0 / 36.0));
+  const V drho36 = A::mul(drho, A::c(1.0 / 36.0));
+  const V musq15 = A::mul(usq, A::c(-1.5));
+  const V k3 = A::fma(usq, A::c(-4.5), A::c(3.0));
+  V uF = A::c(0.0);
+  if (FORCE) {
+    uF = A::mul(u[0], A::c(c.F[0]));
+    uF = A::fma(u[1], A::c(c.F[1]), uF);
+    if (L::D == 3) uF = A::fma(u[2], A::c(c.F[2]), uF);
+  }
+
+  // rest velocity: f_eq0 - w0 rho0 = w0 (drho - 1.5 rho u^2)
+  const V feq0 = A::mul(A::c(L::w(0)), A::fma(rho, musq15, drho));
+  const V np0 = A::sub(g[0], feq0);
+
+  // ---- per pair: equilibrium parts, fneq+-, sources
+  V fs[Q], fa[Q], np[Q], nm[Q], eu[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!is_pair_rep<L>(i)) continue;
+    const int w36 = L::w36(i);
+    eu[i] = edot<L, V>(i, u);
+    const V q = A::mul(eu[i], eu[i]);
+    const V t = A::fma(A::c(4.5), q, musq15);
+    const V t2 = A::fma(A::c(4.5), q, k3);
+    const V wr = w36 == 1 ? rho36 : A::mul(rho36, A::c(double(w36)));
+    const V wd = w36 == 1 ? drho36 : A::mul(drho36, A::c(double(w36)));
+    fs[i] = A::fma(wr, t, wd);                  // symmetric part of the shifted f_eq
+    fa[i] = A::mul(A::mul(wr, eu[i]), t2);      // antisymmetric part
+    np[i] = A::sub(A::mul(A::c(0.5), s[i]), fs[i]);
+    nm[i] = A::sub(A::mul(A::c(0.5), d[i]), fa[i]);
+  }
+
+  // ---- symmetric relaxation target R2
+  V r2[Q];
+  V r20;
+  if constexpr (COLL == C_TRT) {
+    r20 = np0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (is_pair_rep<L>(i)) r2[i] = np[i];
+  } else if constexpr (COLL == C_P_TRT) {
+    using Gh = GhostT<L>;
+    V m[Gh::NG];
+#pragma unroll
+    for (int k = 0; k < Gh::NG; ++k) {
+      // sum_j G(k,j) fneq_j with fneq_i + fneq_ibar = 2 np_i
+      V acc = Gh::G(k, 0) == 0 ? A::c(0.0) : A::mul(A::c(double(Gh::G(k, 0))), np0);
+      bool init = Gh::G(k, 0) != 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i) || Gh::G(k, i) == 0) continue;
+        acc = init ? A::fma(A::c(double(2 * Gh::G(k, i))), np[i], acc)
+                   : A::mul(A::c(double(2 * Gh::G(k, i))), np[i]);
+        init = true;
+      }
+      m[k] = acc;
+    }
+    V pg0 = A::c(0.0);
+    bool init0 = false;
+#pragma unroll
+    for (int k = 0; k < Gh::NG; ++k) {
+      if (Gh::G(k, 0) == 0) continue;
+      const V cc = A::c(L::w(0) * Gh::G(k, 0) * Gh::coef(k));
+      pg0 = init0 ? A::fma(cc, m[k], pg0) : A::mul(cc, m[k]);
+      init0 = true;
+    }
+    r20 = A::sub(np0, pg0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      V pg = A::c(0.0);
+      bool init = false;
+#pragma unroll
+      for (int k = 0; k < Gh::NG; ++k) {
+        if (Gh::G(k, i) == 0) continue;
+        const V cc = A::c(L::w(i) * Gh::G(k, i) * Gh::coef(k));
+        pg = init ? A::fma(cc, m[k], pg) : A::mul(cc, m[k]);
+        init = true;
+      }
+      r2[i] = A::sub(np[i], pg);
+    }
+  } else {
+    // TRT-RLB: w-orthogonal projection onto span{H2}:
+    // A2_ab = sum_i (e_a e_b - cs^2 d_ab) fneq_i; R2_i = 4.5 w_i [sum_a H2_i,aa A_aa + 2 sum_{a<b} e_a e_b A_ab]
+    V Ad[3], Ao[3];  // diagonal xx, yy, zz and off-diagonal xy, xz, yz
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Ad[a] = A::mul(A::c(-1.0 / 3.0), np0);
+      Ao[a] = A::c(0.0);
+    }
+    bool oinit[3] = {false, false, false};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) {
+        const int e = ecomp<L>(i, a);
+        Ad[a] = A::fma(A::c(2.0 * (e * e - 1.0 / 3.0)), np[i], Ad[a]);
+      }
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+        if (b >= L::D) continue;
+        const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+        if (eab == 0) continue;
+        Ao[o] = oinit[o] ? A::fma(A::c(2.0 * eab), np[i], Ao[o]) : A::mul(A::c(2.0 * eab), np[i]);
+        oinit[o] = true;
+      }
+    }
+    V tr = A::add(Ad[0], Ad[1]);
+    if (L::D == 3) tr = A::add(tr, Ad[2]);
+    r20 = A::mul(A::c(4.5 * L::w(0) * (-1.0 / 3.0)), tr);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      V h = A::mul(A::c(ecomp<L>(i, 0) * ecomp<L>(i, 0) - 1.0 / 3.0), Ad[0]);
+#pragma unroll
+      for (int a = 1; a < L::D; ++a) {
+        const int e = ecomp<L>(i, a);
+        h = A::fma(A::c(e * e - 1.0 / 3.0), Ad[a], h);
+      }
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+        if (b >= L::D) continue;
+        const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+        if (eab != 0) h = A::fma(A::c(2.0 * eab), Ao[o], h);
+      }
+      r2[i] = A::mul(A::c(4.5 * L::w(i)), h);
+    }
+  }
+
+  // ---- antisymmetric relaxation target R3 and post-collision
+  V r3[Q];
+  if constexpr (COLL == C_TRT_RLB) {
+    // fneq_i - fneq_ibar = 2 nm_i; modes m_ab = e_a (e_b^2 - cs^2)
+    auto mode = [](int a, int b, int i) constexpr -> double {
+      const int ea = ecomp<L>(i, a), eb = ecomp<L>(i, b);
+      return ea * (eb * eb - 1.0 / 3.0);
+    };
+    if constexpr (L::D == 2) {
+      V Axyy = A::c(0.0), Axxy = A::c(0.0);
+      bool i1 = false, i2 = false;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+        if (mode(0, 1, i) != 0.0) {
+          Axyy = i1 ? A::fma(A::c(2.0 * mode(0, 1, i)), nm[i], Axyy) : A::mul(A::c(2.0 * mode(0, 1, i)), nm[i]);
+          i1 = true;
+        }
+        if (mode(1, 0, i) != 0.0) {
+          Axxy = i2 ? A::fma(A::c(2.0 * mode(1, 0, i)), nm[i], Axxy) : A::mul(A::c(2.0 * mode(1, 0, i)), nm[i]);
+          i2 = true;
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+        V h = A::c(0.0);
+        bool hi = false;
+        if (mode(0, 1, i) != 0.0) {
+          h = A::mul(A::c(13.5 * L::w(i) * mode(0, 1, i)), Axyy);
+          hi = true;
+        }
+        if (mode(1, 0, i) != 0.0)
+          h = hi ? A::fma(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy, h)
+                 : A::mul(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy);
+        r3[i] = h;
+      }
+    } else {
+      V As[3], Adf[3];
+      bool is[3] = {false, false, false}, id[3] = {false, false, false};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        As[a] = A::c(0.0);
+        Adf[a] = A::c(0.0);
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+          const double sv = mode(a, b, i) + mode(a, cc, i);
+          const double dv = mode(a, b, i) - mode(a, cc, i);
+          if (sv != 0.0) {
+            As[a] = is[a] ? A::fma(A::c(2.0 * sv), nm[i], As[a]) : A::mul(A::c(2.0 * sv), nm[i]);
+            is[a] = true;
+          }
+          if (dv != 0.0) {
+            Adf[a] = id[a] ? A::fma(A::c(2.0 * dv), nm[i], Adf[a]) : A::mul(A::c(2.0 * dv), nm[i]);
+            id[a] = true;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+        V h = A::c(0.0);
+        bool hi = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+          const double sv = mode(a, b, i) + mode(a, cc, i);
+          const double dv = mode(a, b, i) - mode(a, cc, i);
+          if (sv != 0.0) {
+            h = hi ? A::fma(A::c(13.5 * L::w(i) * sv), As[a], h) : A::mul(A::c(13.5 * L::w(i) * sv), As[a]);
+            hi = true;
+          }
+          if (dv != 0.0) {
+            h = hi ? A::fma(A::c(4.5 * L::w(i) * dv), Adf[a], h) : A::mul(A::c(4.5 * L::w(i) * dv), Adf[a]);
+            hi = true;
+          }
+        }
+        r3[i] = h;
+      }
+    }
+  }
+
+  // rest: f*_0 = f_eq0 + (1 - w+) R2_0 + S+_0, S+_0 = hg w0 (-3 u.F)
+  V g0 = A::fma(A::c(c.cp), r20, feq0);
+  if (FORCE) g0 = A::fma(A::c(c.fu[0]), uF, g0);
+  g[0] = g0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!is_pair_rep<L>(i)) continue;
+    V sym = A::fma(A::c(c.cp), r2[i], fs[i]);
+    V anti;
+    if constexpr (COLL == C_TRT_RLB) {
+      anti = A::fma(A::c(c.cm), r3[i], fa[i]);
+    } else {
+      anti = A::fma(A::c(c.cm), nm[i], fa[i]);
+    }
+    if (FORCE) {
+      // S+_i = hg w (9 eu eF - 3 u.F); antisymmetric force: F_i/2 + (1 - w-) F_i/2
+      // (P-TRT, TRT) or F_i/2 (TRT-RLB, whose R3 already carries the first-order part)
+      sym = A::fma(A::c(c.fe[i]), eu[i], sym);
+      sym = A::fma(A::c(c.fu[i]), uF, sym);
+      anti = A::add(anti, A::c(c.fa[i]));
+    }
+    g[i] = A::add(sym, anti);
+    g[L::opp(i)] = A::sub(sym, anti);
+  }
+  return badmask;
+}
+
+}  // namespace lbm

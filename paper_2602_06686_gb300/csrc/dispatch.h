@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "collide_v.cuh"
+
 namespace lbm {
 
 struct GeoH {
@@ -14,15 +16,23 @@ struct GeoH {
 };
 
 struct Variant {
-  int nv;  // nodes per thread along x
-  int bx;  // threads per block along x (multiple of 32)
-  int by;  // rows per block
+  int kind;    // 0: register kernel (one warp row per block row), 1: bulk-copy pipelined kernel
+  int nv;      // kind 0: nodes per thread along x
+  int bx;      // kind 0: threads per block along x (multiple of 32)
+  int by;      // kind 0: rows per block
+  int X;       // kind 1: tile width (nodes)
+  int stages;  // kind 1: shared-memory ring depth
 };
 
 struct StepLaunch {
   GeoH g;
   int collision;  // 0 TRT, 1 TRT-RLB, 2 P-TRT (BGK / RLB mapped by the caller)
-  double rho0, cp, cm, hg, F[3];
+  bool force;     // any force component non-zero
+  CoefV<double> c;
+  int* err;       // bounded-wait error word
+  long long wait_ns;  // limit of each bounded wait (pipelined kernel)
+  int extra_tx;       // test hook: bytes a stage waits for that never arrive
+  int sms;        // multiprocessors of the device
   const void* src;
   void* dst;
   const uint8_t* mask;
@@ -47,7 +57,8 @@ struct AuxLaunch {
 // Per-lattice descriptor and tile of the persistent batched kernel.
 struct BatchDesc {
   GeoH g;
-  double rho0, cp, cm, hg, F[3];
+  CoefV<double> cd;
+  CoefV<float> cf;
   long long off;  // byte offset of the lattice in each population arena
 };
 struct BatchTile {
@@ -84,7 +95,49 @@ struct Ops {
   // persistent batched kernel (cooperative launch) and its occupancy
   cudaError_t (*batch)(const BatchLaunch&);
   int (*batch_blocks_per_sm)(int collision, int threads);
+  // shared-memory bytes of the pipelined kernel for a tile width and ring depth (0: unsupported)
+  size_t (*tma_smem)(int X, int stages);
 };
+
+// Per-direction collision constants from the rates and the force (host, FP64).
+template <class L>
+inline void fill_coef(double rho0, double wp, double wm_run, int collision, const double F[3],
+                      CoefV<double>* c) {
+  *c = CoefV<double>{};
+  c->rho0 = rho0;
+  c->cp = 1.0 - wp;
+  c->cm = 1.0 - wm_run;
+  const double hg = 1.0 - 0.5 * wp;
+  for (int a = 0; a < 3; ++a) {
+    c->Fh[a] = 0.5 * F[a];
+    c->F[a] = F[a];
+  }
+  for (int i = 0; i < L::Q; ++i) {
+    const double eF = L::cx(i) * F[0] + L::cy(i) * F[1] + L::cz(i) * F[2];
+    const double w = L::w(i);
+    c->fe[i] = 9.0 * w * eF * hg;
+    c->fu[i] = -3.0 * w * hg;
+    c->fa[i] = collision == 1 ? 1.5 * w * eF : 1.5 * w * eF * (2.0 - wm_run);
+  }
+}
+
+template <typename R>
+inline CoefV<R> coef_cast(const CoefV<double>& d) {
+  CoefV<R> c;
+  c.rho0 = R(d.rho0);
+  c.cp = R(d.cp);
+  c.cm = R(d.cm);
+  for (int a = 0; a < 3; ++a) {
+    c.Fh[a] = R(d.Fh[a]);
+    c.F[a] = R(d.F[a]);
+  }
+  for (int i = 0; i < kQMax; ++i) {
+    c.fe[i] = R(d.fe[i]);
+    c.fu[i] = R(d.fu[i]);
+    c.fa[i] = R(d.fa[i]);
+  }
+  return c;
+}
 
 const Ops* ops_d2q9_f64();
 const Ops* ops_d2q9_f32();

@@ -12,6 +12,7 @@ namespace lbm {
 
 // Scratch buffer layout (bytes).
 constexpr size_t kFlagOffset = 0;        // unsigned int: earliest diverged step (0xffffffff: none)
+constexpr size_t kErrOffset = 64;        // int: 1 when a bounded device wait ran out
 constexpr size_t kBarrierOffset = 256;   // batch grid-barrier words and error status
 constexpr size_t kPartialOffset = 4096;  // double [kMaxPartials][8] block partials
 constexpr int kMaxPartials = 4096;
@@ -27,10 +28,12 @@ struct Plan {
   double omega_plus, omega_minus;
   int kernel_collision;  // collision the kernels run (BGK -> TRT, RLB -> P-TRT)
   double cp, cm, hg;     // 1 - w+, 1 - w- (as run), 1 - w+/2
+  bool force;            // any force component non-zero
+  CoefV<double> coef;    // per-direction collision constants (FP64)
 };
 
 int plan(const lbm_params* p, Plan* out);
-std::vector<Variant> variants_for(const Plan& pl, const Ops* ops);
+std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked);
 int default_variant(const Plan& pl, const std::vector<Variant>& vs);
 
 int ctx_new(const Plan& pl, cudaStream_t st, lbm_ctx** out);

@@ -22,7 +22,7 @@
 #pragma once
 #include <stdint.h>
 
-#include "collide.cuh"
+#include "collide_v.cuh"
 #include "lattice.cuh"
 #include "storage.cuh"
 
@@ -38,13 +38,29 @@ struct Geo {
 template <typename R>
 struct StepArgs {
   Geo g;
-  Coef<R> c;
+  CoefV<R> c;
   const void* src;
   void* dst;
   const uint8_t* mask;  // [nz][ny][nx] or null
   unsigned int* flag;   // divergence: earliest step index seen (atomicMin; 0xffffffff = none)
   unsigned int step;    // index of the step being computed
 };
+
+__device__ __forceinline__ unsigned lane_id() {
+  unsigned l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+
+// Records `step` as a divergence step: one atomic per warp, and none once the
+// flag already holds an earlier (or equal) step.
+__device__ __forceinline__ void record_bad(unsigned int* flag, unsigned int step, bool bad) {
+  const unsigned m = __activemask();
+  const unsigned b = __ballot_sync(m, bad);
+  if (b != 0u && lane_id() == (unsigned)(__ffs(b) - 1)) {
+    if (*reinterpret_cast<volatile unsigned int*>(flag) > step) atomicMin(flag, step);
+  }
+}
 
 template <typename R>
 __device__ __forceinline__ R shfl_up1(R v) {
@@ -157,8 +173,7 @@ __device__ __forceinline__ void update_chunk(const StepArgs<typename S::R>& a, i
     R g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) g[i] = f[i][k];
-    bool bad;
-    collide<L, COLL, R>(g, a.c, bad);
+    const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
     anybad |= bad && !solid[k];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) f[i][k] = g[i];
@@ -174,13 +189,13 @@ __device__ __forceinline__ void update_chunk(const StepArgs<typename S::R>& a, i
 #pragma unroll
         for (int k = 0; k < NV; ++k)
           if (!solid[k]) dst[i * G.plane + own + k] = S::enc(f[i][k]);
-      if (anybad) atomicMin(a.flag, a.step);
+      record_bad(a.flag, a.step, anybad);
       return;
     }
   }
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) st_enc<S, NV>(dst + i * G.plane + own, f[i]);
-  if (anybad) atomicMin(a.flag, a.step);
+  record_bad(a.flag, a.step, anybad);
 }
 
 // Grid: x = ceil(nx / (NV * blockDim.x)) chunks-blocks, y = ceil(ny / blockDim.y), z = nz.

@@ -5,6 +5,7 @@
 #include "kernels.cuh"
 #include "aa.cuh"
 #include "batch.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 
@@ -138,11 +139,7 @@ struct TU {
   static StepArgs<R> args(const StepLaunch& s) {
     StepArgs<R> a;
     a.g = geo(s.g);
-    a.c.rho0 = R(s.rho0);
-    a.c.cp = R(s.cp);
-    a.c.cm = R(s.cm);
-    a.c.hg = R(s.hg);
-    for (int k = 0; k < 3; ++k) a.c.F[k] = R(s.F[k]);
+    a.c = coef_cast<R>(s.c);
     a.src = s.src;
     a.dst = s.dst;
     a.mask = s.mask;
@@ -171,6 +168,76 @@ struct TU {
     return cudaGetLastError();
   }
 
+  // ---- pipelined bulk-copy kernel (kind 1)
+  static constexpr bool kPack = sizeof(R) == 4;
+  static int halo() { return 16 / (int)sizeof(T); }
+  static size_t tma_smem(int X, int stages) {
+    const int H = halo();
+    if (X <= 0 || stages < 2 || X % (2 * H) != 0) return 0;
+    const size_t head = 128 * ((2 * (size_t)stages * 8 + 4 + 127) / 128);
+    return head + (size_t)stages * L::Q * (size_t)(X + 2 * H) * sizeof(T);
+  }
+
+  template <int COLL, bool FORCE>
+  static cudaError_t go_tma(const StepLaunch& s) {
+    TmaArgs<R> a;
+    a.g = geo(s.g);
+    a.c = coef_cast<R>(s.c);
+    a.src = s.src;
+    a.dst = s.dst;
+    a.flag = s.flag;
+    a.err = s.err;
+    a.step = s.step;
+    a.H = halo();
+    const int Xmax = s.v.X;
+    const int ntx = (s.g.nx + Xmax - 1) / Xmax;
+    // equal tiles, each a multiple of 2H
+    int X = (s.g.nx + ntx - 1) / ntx;
+    X = (X + 2 * a.H - 1) / (2 * a.H) * (2 * a.H);
+    a.X = X;
+    a.ntx = (s.g.nx + X - 1) / X;
+    a.stages = s.v.stages;
+    a.slot = X + 2 * a.H;
+    a.ntiles = (long long)a.ntx * s.g.ny * s.g.nz;
+    a.timeout_ns = s.wait_ns > 0 ? s.wait_ns : 2000000000LL;
+    a.extra_tx = s.extra_tx;
+    const size_t smem = tma_smem(X, a.stages);
+    if (smem == 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    auto kern = &k_step_tma<L, COLL, S, FORCE, kPack>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long blocks = (long long)per_sm * (s.sms > 0 ? s.sms : 1);
+    if (blocks > a.ntiles) blocks = a.ntiles;
+    kern<<<(unsigned)blocks, kTmaThreads, smem, s.stream>>>(a);
+    return cudaGetLastError();
+  }
+
+  template <int COLL>
+  static cudaError_t tma_coll(const StepLaunch& s) {
+    return s.force ? go_tma<COLL, true>(s) : go_tma<COLL, false>(s);
+  }
+
+  static cudaError_t step_tma(const StepLaunch& s) {
+    if (s.mask != nullptr || s.layout != 0) return cudaErrorInvalidValue;
+    switch (s.collision) {
+      case C_TRT:
+        return tma_coll<C_TRT>(s);
+      case C_TRT_RLB:
+        return tma_coll<C_TRT_RLB>(s);
+      case C_P_TRT:
+        return tma_coll<C_P_TRT>(s);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   template <int NV>
   static cudaError_t step_nv(const StepLaunch& s) {
     const bool m = s.mask != nullptr;
@@ -186,6 +253,7 @@ struct TU {
   }
 
   static cudaError_t step(const StepLaunch& s) {
+    if (s.v.kind == 1) return step_tma(s);
     switch (s.v.nv) {
       case 1:
         return step_nv<1>(s);
@@ -291,6 +359,7 @@ struct TU {
       r.macros = &macros;
       r.batch = &batch;
       r.batch_blocks_per_sm = &batch_blocks_per_sm;
+      r.tma_smem = &tma_smem;
       return r;
     }();
     return &o;

@@ -30,7 +30,7 @@ EXPORTED = [
     "lbm_bind_buffers", "lbm_init_equilibrium", "lbm_init_equilibrium_host", "lbm_step",
     "lbm_macros", "lbm_macros_host", "lbm_get_populations", "lbm_set_populations",
     "lbm_diagnostics", "lbm_velocity_l2", "lbm_status", "lbm_step_count", "lbm_checkpoint",
-    "lbm_restore", "lbm_launch_count", "lbm_variant_count", "lbm_variant_name",
+    "lbm_restore", "lbm_launch_count", "lbm_set_wait_limit", "lbm_variant_count", "lbm_variant_name",
     "lbm_get_variant", "lbm_set_variant", "lbm_autotune", "lbm_destroy", "lbm_copy_ceiling",
     "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind", "lbm_batch_lattice",
     "lbm_batch_step", "lbm_batch_variant_count", "lbm_batch_variant_name",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_checkpoint": ([vp, vp, sz, ll], ctypes.c_int),
         "lbm_restore": ([vp, vp, sz, ctypes.c_longlong], ctypes.c_int),
         "lbm_launch_count": ([vp, ll], ctypes.c_int),
+        "lbm_set_wait_limit": ([vp, ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "lbm_variant_count": ([vp, ip], ctypes.c_int),
         "lbm_variant_name": ([vp, ctypes.c_int, ctypes.c_char_p, sz], ctypes.c_int),
         "lbm_get_variant": ([vp, ip], ctypes.c_int),
@@ -311,6 +312,10 @@ class Lattice:
         buf, t = snap
         _check(self.lib.lbm_restore(self.ctx, _dev_ptr(buf), self.pop_bytes, int(t)),
                "lbm_restore")
+
+    def set_wait_limit(self, seconds: float, test_extra_bytes: int = 0):
+        _check(self.lib.lbm_set_wait_limit(self.ctx, float(seconds), int(test_extra_bytes)),
+               "lbm_set_wait_limit")
 
     # -- kernel variants
     def variants(self):

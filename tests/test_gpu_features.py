@@ -199,3 +199,32 @@ def test_invalid_arguments_raise():
     g = gpu_lattice(O.D2Q9, (1, 8, 8), O.P_TRT, 0.1, 0.25)
     with pytest.raises(LBMError):
         g.step(-1)
+
+
+def test_pipelined_kernel_wait_runs_out_and_reports():
+    """The pipelined kernel's stage waits are bounded: when every stage waits
+    for bytes that never arrive (test hook), each wait gives up after the limit,
+    the kernel returns and lbm_status reports LBM_ERR_TIMEOUT; with the hook off
+    the same context steps normally again."""
+    shape = (1, 16, 256)
+    rng = np.random.default_rng(37)
+    rho, u = W.random_macros(shape, 2, rng)
+    g = gpu_lattice(O.D2Q9, shape, O.P_TRT, 0.03, 0.25, storage="F32")
+    names = g.variants()
+    g.variant = next(v for v, n in enumerate(names) if n.startswith("tma"))
+    g.init_equilibrium(rho, u)
+    g.set_wait_limit(0.2, test_extra_bytes=16)
+    g.step(1)
+    from paper_2602_06686_gb300 import LBMError
+    with pytest.raises(LBMError) as e:
+        g.status()
+    assert e.value.code == -4
+    g.set_wait_limit(2.0, 0)
+    g.init_equilibrium(rho, u)
+    g.step(3)
+    assert g.status()[0] == 0
+    ref = gpu_lattice(O.D2Q9, shape, O.P_TRT, 0.03, 0.25, storage="F32")
+    ref.variant = next(v for v, n in enumerate(ref.variants()) if not n.startswith("tma"))
+    ref.init_equilibrium(rho, u)
+    ref.step(3)
+    assert np.array_equal(g.populations().cpu().numpy(), ref.populations().cpu().numpy())
