@@ -36,6 +36,9 @@
 //
 // Every operation is an explicitly rounded add / sub / mul / fma, so the scalar
 // and packed paths give bit-identical results and the compiler cannot regroup.
+// No inexact product feeds a separate addition: the optimiser fuses such pairs
+// in the packed form (the scalar intrinsics are left alone), so every product
+// that is summed is written as an fma here.
 #pragma once
 #include <string.h>
 
@@ -323,29 +326,24 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
       }
       m[k] = acc;
     }
-    V pg0 = A::c(0.0);
-    bool init0 = false;
+    // R2_i = np_i - sum_k w_i G(k,i) (s_k^2/N_k) m_k as one fma chain from np_i (no
+    // product feeds a separate subtraction, so there is nothing left to contract)
+    r20 = np0;
 #pragma unroll
     for (int k = 0; k < Gh::NG; ++k) {
       if (Gh::G(k, 0) == 0) continue;
-      const V cc = A::c(L::w(0) * Gh::G(k, 0) * Gh::coef(k));
-      pg0 = init0 ? A::fma(cc, m[k], pg0) : A::mul(cc, m[k]);
-      init0 = true;
+      r20 = A::fma(A::c(-L::w(0) * Gh::G(k, 0) * Gh::coef(k)), m[k], r20);
     }
-    r20 = A::sub(np0, pg0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (!is_pair_rep<L>(i)) continue;
-      V pg = A::c(0.0);
-      bool init = false;
+      V r = np[i];
 #pragma unroll
       for (int k = 0; k < Gh::NG; ++k) {
         if (Gh::G(k, i) == 0) continue;
-        const V cc = A::c(L::w(i) * Gh::G(k, i) * Gh::coef(k));
-        pg = init ? A::fma(cc, m[k], pg) : A::mul(cc, m[k]);
-        init = true;
+        r = A::fma(A::c(-L::w(i) * Gh::G(k, i) * Gh::coef(k)), m[k], r);
       }
-      r2[i] = A::sub(np[i], pg);
+      r2[i] = r;
     }
   } else {
     // TRT-RLB: w-orthogonal projection onto span{H2}:
