@@ -181,6 +181,31 @@ int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
  * |u| > 1; *first_step (may be NULL) receives the earliest such step or -1. */
 int lbm_status(lbm_ctx* ctx, long long* first_step);
 
+/* Diagnostics without a scratch buffer (the paper has no counterpart; this is
+ * a library facility).  For callers that cannot allocate device memory for
+ * lbm_bind_buffers' scratch: for example a program whose device memory belongs
+ * to another framework's pool, or a tool attached to a running simulation that
+ * must not grow its footprint.  It computes the eight values of
+ * lbm_diagnostics for the state held in `pop_state` and writes them to `out`
+ * (device, 8 FP64) asynchronously on `cuda_stream`:
+ *   p           the lattice's parameters (as given to lbm_create);
+ *   pop_state   device buffer holding the current state: for the A/B layout
+ *               the buffer the next step reads (pop_a after an even number of
+ *               steps since initialisation, pop_b after an odd one), for AA the
+ *               single buffer;
+ *   solid_mask  device uint8 [nz][ny][nx] or NULL, as bound to the context;
+ *   steps_done  steps completed since initialisation (selects the AA slot
+ *               rule and is stored in out[7]).
+ * It allocates nothing: its working memory is one fixed array of about 8.4 MB
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  Lattices of more than 262144 nodes (e.g. 512 x 512, 64^3) are
+ * rejected with LBM_ERR_ARG.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the array, so calls whose
+ * work overlaps on the GPU race; the array keeps the last call's contents. */
+int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_state, const uint8_t* solid_mask,
+                            long long steps_done, double* out, void* cuda_stream);
+
 /* Number of completed time steps since initialisation. */
 int lbm_step_count(const lbm_ctx* ctx, long long* t);
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind", "lbm_batch_lattice",
     "lbm_batch_step", "lbm_batch_variant_count", "lbm_batch_variant_name",
     "lbm_batch_set_variant", "lbm_batch_autotune", "lbm_batch_set_barrier",
-    "lbm_batch_launches", "lbm_batch_destroy",
+    "lbm_batch_launches", "lbm_batch_destroy", "lbm_diagnostics_noalloc",
 ]
 
 
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_batch_set_barrier": ([vp, ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "lbm_batch_launches": ([vp, ll], ctypes.c_int),
         "lbm_batch_destroy": ([vp], ctypes.c_int),
+        "lbm_diagnostics_noalloc": ([pp, vp, vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
