@@ -125,12 +125,12 @@ std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked) {
   // pipelined bulk-copy kernel: A/B layout, no solid mask, rows a multiple of 16 bytes
   const int H = 16 / pl.esize;
   if (pl.p.layout == LBM_LAYOUT_AB && !masked && pl.p.nx % H == 0 && pl.p.nx >= 2 * H) {
-    static const int tiles[] = {256, 512, 128};
-    static const int depths[] = {4, 6, 3, 8};
+    static const int tiles[] = {512, 384, 256, 192, 128};
+    static const int depths[] = {4, 3, 6, 8, 2};
     for (int X : tiles)
       for (int st : depths) {
         const size_t smem = ops->tma_smem(X, st);
-        if (smem > 0 && smem <= 110 * 1024) v.push_back(Variant{1, 0, 0, 0, X, st});
+        if (smem > 0 && smem <= 200 * 1024) v.push_back(Variant{1, 0, 0, 0, X, st});
       }
   }
   for (int k = 0; k < ops->n_nv; ++k) {

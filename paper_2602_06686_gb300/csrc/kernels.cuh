@@ -170,13 +170,33 @@ __device__ __forceinline__ void update_chunk(const StepArgs<typename S::R>& a, i
   for (int k = 0; k < NV; ++k) {
     solid[k] = false;
     if constexpr (MASK) solid[k] = a.mask[((long long)z * G.ny + y) * G.nx + x0 + k] != 0;
-    R g[L::Q];
+  }
+  if constexpr (sizeof(R) == 4 && NV % 2 == 0) {
+    // FP32 arithmetic, two nodes at a time with the packed f32x2 instructions
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) g[i] = f[i][k];
-    const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
-    anybad |= bad && !solid[k];
+    for (int k = 0; k < NV; k += 2) {
+      F2 g[L::Q];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i][k] = g[i];
+      for (int i = 0; i < L::Q; ++i) g[i] = F2{f[i][k], f[i][k + 1]};
+      const unsigned bad = collide_v<L, COLL, true, F2>(g, a.c);
+      anybad |= ((bad & 1u) && !solid[k]) || ((bad & 2u) && !solid[k + 1]);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        f[i][k] = g[i].x;
+        f[i][k + 1] = g[i].y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      R g[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) g[i] = f[i][k];
+      const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
+      anybad |= bad && !solid[k];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) f[i][k] = g[i];
+    }
   }
   const long long own = ((long long)z * G.ny + y) * G.pitch + x0;
   if constexpr (MASK) {

@@ -14,7 +14,10 @@
 // bytes in flight per SM are set by the ring size, not by occupancy.
 //
 // FP32 / FP16 / BF16 storage: each consumer thread advances two nodes (x and
-// x + X/2) with the packed f32x2 arithmetic (collide_v<..., F2>).
+// x + X/2) with the packed f32x2 arithmetic (collide_v<..., F2>).  The tile
+// width X is a compile-time constant, so in tiles without walls every shared
+// read is a single load at a fixed offset; consumers release the stage as soon
+// as their populations are in registers, before colliding.
 //
 // Rows whose source lies beyond a non-periodic wall (halfway bounce-back) are
 // replaced by the node's own row of the opposite plane; x-walls read the
@@ -34,8 +37,17 @@
 
 namespace lbm {
 
-constexpr int kTmaConsumerWarps = 4;
-constexpr int kTmaThreads = 32 * (1 + kTmaConsumerWarps);
+// One producer warp plus X / NPT consumer threads (NPT = 2 nodes per thread with
+// the packed arithmetic, 1 otherwise): every consumer thread owns one node pair
+// (x0 + j, x0 + j + X/2) -- or one node -- of each tile.
+template <int X, bool PACK>
+struct TmaShape {
+  static constexpr int kNPT = PACK ? 2 : 1;
+  static constexpr int kConsumers = X / kNPT;
+  static constexpr int kConsumerWarps = kConsumers / 32;
+  static constexpr int kThreads = 32 + kConsumers;
+  static_assert(kConsumers % 32 == 0, "tile width must give whole consumer warps");
+};
 
 template <typename R>
 struct TmaArgs {
@@ -46,12 +58,9 @@ struct TmaArgs {
   unsigned int* flag;  // divergence: earliest step (atomicMin)
   int* err;            // set to 1 when a bounded wait runs out
   unsigned int step;
-  int X;       // tile width (nodes), a multiple of 2H
-  int H;       // halo (elements) = 16 bytes
   int stages;  // ring depth
-  int ntx;     // tiles per row
-  long long ntiles;
-  int slot;    // elements per plane slot = X + 2H
+  int ntx;     // tiles per row (tile width is the kernel's compile-time X)
+  int ntiles;  // ntx * ny * nz (< 2^31)
   long long timeout_ns;
   int extra_tx;  // test hook: extra bytes every stage waits for (never delivered)
 };
@@ -134,6 +143,32 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity,
   }
 }
 
+// The contiguous chunk of tiles [begin, end) owned by this block, walked with
+// incremental (tx, y, z) coordinates (no divisions inside the loop).  Tiles are
+// numbered ((z * ny) + y) * ntx + tx.
+struct TileWalk {
+  int t, end, tx, y, z, ntx, ny;
+  __device__ __forceinline__ TileWalk(int ntiles, int ntx_, int ny_) : ntx(ntx_), ny(ny_) {
+    t = (int)(((long long)ntiles * blockIdx.x) / gridDim.x);
+    end = (int)(((long long)ntiles * (blockIdx.x + 1)) / gridDim.x);
+    tx = t % ntx;
+    const int row = t / ntx;
+    y = row % ny;
+    z = row / ny;
+  }
+  __device__ __forceinline__ bool more() const { return t < end; }
+  __device__ __forceinline__ void next() {
+    ++t;
+    if (++tx == ntx) {
+      tx = 0;
+      if (++y == ny) {
+        y = 0;
+        ++z;
+      }
+    }
+  }
+};
+
 template <class L>
 __device__ __forceinline__ void tma_source_row(const Geo& G, int i, int y, int z, int& ys, int& zs,
                                                bool& wall) {
@@ -150,11 +185,15 @@ __device__ __forceinline__ void tma_source_row(const Geo& G, int i, int y, int z
   }
 }
 
-template <class L, int COLL, class S, bool FORCE, bool PACK>
-__global__ void __launch_bounds__(kTmaThreads) k_step_tma(const TmaArgs<typename S::R> a) {
+template <class L, int COLL, class S, bool FORCE, bool PACK, int XT>
+__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
+    k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
   using V = typename std::conditional<PACK, F2, R>::type;
+  using Sh = TmaShape<XT, PACK>;
+  constexpr int HT = 16 / (int)sizeof(T);  // halo (elements)
+  constexpr int SLOT = XT + 2 * HT;        // elements per plane slot
   extern __shared__ __align__(128) unsigned char smem[];
   const Geo& G = a.g;
   const int ST = a.stages;
@@ -162,12 +201,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const TmaArgs<typename
   uint64_t* empty = full + ST;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + ST);
   T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
-  const long long stage_elems = (long long)L::Q * a.slot;
+  constexpr long long stage_elems = (long long)L::Q * SLOT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_addr(full + s), 1);
-      mbar_init(smem_addr(empty + s), kTmaConsumerWarps);
+      mbar_init(smem_addr(empty + s), Sh::kConsumerWarps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -181,28 +220,27 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const TmaArgs<typename
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane != 0) return;
-    long long k = 0;
+    TileWalk w(a.ntiles, a.ntx, G.ny);
+    int k = 0;
+    int s = 0;       // stage of tile k
+    uint32_t u = 0;  // use count of stage s
     bool ok = true;
-    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
-      const int s = (int)(k % ST);
-      const long long u = k / ST;
-      if (u > 0 && !mbar_wait(smem_addr(empty + s), (uint32_t)((u - 1) & 1), abort_flag, a.err,
+    for (; w.more(); w.next(), ++k) {
+      if (u > 0 && !mbar_wait(smem_addr(empty + s), (u - 1) & 1u, abort_flag, a.err,
                                a.timeout_ns)) {
         ok = false;
         break;
       }
-      const int tx = (int)(t % a.ntx);
-      const long long row = t / a.ntx;
-      const int y = (int)(row % G.ny), z = (int)(row / G.ny);
-      const int x0 = tx * a.X;
-      const int xe = min(x0 + a.X, G.nx);  // end of the tile's nodes
+      const int y = w.y, z = w.z;
+      const int x0 = w.tx * XT;
+      const int xe = min(x0 + XT, G.nx);  // end of the tile's nodes
       // copy window [lo, hi) of every source row, plus wrap halos at row ends
-      const int lo = max(x0 - a.H, 0);
-      const int hi = min(xe + a.H, G.nx);
+      const int lo = max(x0 - HT, 0);
+      const int hi = min(xe + HT, G.nx);
       const bool lwrap = G.per[0] && x0 == 0;
       const bool rwrap = G.per[0] && xe == G.nx;
       const uint32_t main_bytes = (uint32_t)(hi - lo) * sizeof(T);
-      const uint32_t halo_bytes = (uint32_t)a.H * sizeof(T);
+      constexpr uint32_t halo_bytes = (uint32_t)HT * sizeof(T);
       uint32_t total = 0;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
@@ -220,72 +258,80 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const TmaArgs<typename
         int ys, zs;
         bool wall;
         tma_source_row<L>(G, i, y, z, ys, zs, wall);
-        T* slot = st + i * a.slot;  // slot[k] holds x = x0 - H + k
+        T* slot = st + i * SLOT;  // slot[k] holds x = x0 - HT + k
         const T* rowp = wall ? src + L::opp(i) * G.plane + ((long long)z * G.ny + y) * G.pitch
                              : src + i * G.plane + ((long long)zs * G.ny + ys) * G.pitch;
-        bulk_g2s(smem_addr(slot + (lo - (x0 - a.H))), rowp + lo, main_bytes, fb);
+        bulk_g2s(smem_addr(slot + (lo - (x0 - HT))), rowp + lo, main_bytes, fb);
         if (!wall) {
-          if (lwrap) bulk_g2s(smem_addr(slot), rowp + G.nx - a.H, halo_bytes, fb);
-          if (rwrap) bulk_g2s(smem_addr(slot + a.H + (G.nx - x0)), rowp, halo_bytes, fb);
+          if (lwrap) bulk_g2s(smem_addr(slot), rowp + G.nx - HT, halo_bytes, fb);
+          if (rwrap) bulk_g2s(smem_addr(slot + HT + (G.nx - x0)), rowp, halo_bytes, fb);
         }
+      }
+      if (++s == ST) {
+        s = 0;
+        ++u;
       }
     }
     if (!ok) {
       // let every issued copy land before the block's shared memory is released
-      for (long long kk = (k > ST ? k - ST : 0); kk < k; ++kk) {
-        const int s = (int)(kk % ST);
-        const long long u = kk / ST;
+      for (int kk = (k > ST ? k - ST : 0); kk < k; ++kk) {
         volatile int dummy = 0;
-        mbar_wait(smem_addr(full + s), (uint32_t)(u & 1), &dummy, a.err, a.timeout_ns);
+        mbar_wait(smem_addr(full + kk % ST), (uint32_t)((kk / ST) & 1), &dummy, a.err, a.timeout_ns);
       }
     }
     return;
   }
 
   // -------------------------------------------------------------- consumers
-  const int ct = threadIdx.x - 32;
-  constexpr int NCT = 32 * kTmaConsumerWarps;
-  long long k = 0;
-  for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
-    const int s = (int)(k % ST);
-    const long long u = k / ST;
-    if (!mbar_wait_warp(smem_addr(full + s), (uint32_t)(u & 1), abort_flag, a.err, a.timeout_ns))
-      break;
-    const int tx = (int)(t % a.ntx);
-    const long long row = t / a.ntx;
-    const int y = (int)(row % G.ny), z = (int)(row / G.ny);
-    const int x0 = tx * a.X;
-    const int wdt = min(a.X, G.nx - x0);
+  constexpr int NPT = Sh::kNPT;
+  const int ct = threadIdx.x - 32;  // 0 .. kConsumers-1: this thread's node (pair)
+  int jn[NPT];
+  jn[0] = ct;
+  if (PACK) jn[NPT - 1] = ct + XT / 2;
+  TileWalk w(a.ntiles, a.ntx, G.ny);
+  int s = 0;
+  uint32_t u = 0;
+  for (; w.more(); w.next()) {
+    if (!mbar_wait_warp(smem_addr(full + s), u & 1u, abort_flag, a.err, a.timeout_ns)) break;
+    const int y = w.y, z = w.z;
+    const int x0 = w.tx * XT;
+    const int wdt = min(XT, G.nx - x0);
     const T* st = ring + s * stage_elems;
     const long long own = ((long long)z * G.ny + y) * G.pitch;
-    bool wallrow[L::Q];
+    // tile-uniform: does any plane's source row lie beyond a wall (|e| <= 1, so
+    // only boundary rows of a non-periodic axis), or does the tile touch an x
+    // wall?  If neither, every read is one shared load at a fixed offset.
+    const bool anywall = (!G.per[1] && (y == 0 || y == G.ny - 1)) ||
+                         (L::D == 3 && !G.per[2] && (z == 0 || z == G.nz - 1));
+    const bool xwall = !G.per[0] && (x0 == 0 || x0 + XT >= G.nx);
+    bool act[NPT];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      int ys, zs;
-      tma_source_row<L>(G, i, y, z, ys, zs, wallrow[i]);
-    }
-    unsigned anybad = 0;
-    constexpr int NPT = PACK ? 2 : 1;
-    const int half = a.X / 2;
-    const int nwork = PACK ? half : a.X;
-    for (int p = ct; p < nwork; p += NCT) {
-      int jn[NPT];
-      jn[0] = p;
-      if (PACK) jn[NPT - 1] = p + half;
-      bool act[NPT];
+    for (int n = 0; n < NPT; ++n) act[n] = jn[n] < wdt;
+    V g[L::Q];
+    if (!anywall && !xwall) {
 #pragma unroll
-      for (int n = 0; n < NPT; ++n) act[n] = jn[n] < wdt;
-      V g[L::Q];
+      for (int i = 0; i < L::Q; ++i) {
+        const T* slot = st + i * SLOT + HT - L::cx(i);
+        if constexpr (PACK) {
+          g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[NPT - 1]])};
+        } else {
+          g[i] = S::dec(slot[jn[0]]);
+        }
+      }
+    } else {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const int ex = L::cx(i);
-        const T* slot = st + i * a.slot + a.H;
+        const T* slot = st + i * SLOT + HT;
+        int ys, zs;
+        bool wallrow;
+        tma_source_row<L>(G, i, y, z, ys, zs, wallrow);
         R v[NPT];
 #pragma unroll
         for (int n = 0; n < NPT; ++n) {
           const int j = jn[n];
           const int x = x0 + j;
-          if (wallrow[i]) {
+          if (wallrow) {
             v[n] = S::dec(slot[j]);
           } else if (!G.per[0] && ((ex == 1 && x == 0) || (ex == -1 && x == G.nx - 1))) {
             v[n] = act[n] ? S::dec(src[L::opp(i) * G.plane + own + x]) : R(0);
@@ -299,23 +345,29 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const TmaArgs<typename
           g[i] = v[0];
         }
       }
-      const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
-      if (act[0] && (bad & 1u)) anybad = 1;
-      if (PACK && act[NPT - 1] && (bad & 2u)) anybad = 1;
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        T* outp = dst + i * G.plane + own + x0;
-        if constexpr (PACK) {
-          if (act[0]) outp[jn[0]] = S::enc(g[i].x);
-          if (act[NPT - 1]) outp[jn[NPT - 1]] = S::enc(g[i].y);
-        } else {
-          if (act[0]) outp[jn[0]] = S::enc(g[i]);
-        }
-      }
     }
+    // the stage is no longer read: release it before computing
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_addr(empty + s));
-    record_bad(a.flag, a.step, anybad != 0u);
+    if (++s == ST) {
+      s = 0;
+      ++u;
+    }
+    const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
+    bool anybad = act[0] && (bad & 1u);
+    if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
+    T* op = dst + own + x0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if constexpr (PACK) {
+        if (act[0]) op[jn[0]] = S::enc(g[i].x);
+        if (act[NPT - 1]) op[jn[NPT - 1]] = S::enc(g[i].y);
+      } else {
+        if (act[0]) op[jn[0]] = S::enc(g[i]);
+      }
+      op += G.plane;
+    }
+    record_bad(a.flag, a.step, anybad);
   }
 }
 

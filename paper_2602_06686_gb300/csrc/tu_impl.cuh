@@ -170,16 +170,19 @@ struct TU {
 
   // ---- pipelined bulk-copy kernel (kind 1)
   static constexpr bool kPack = sizeof(R) == 4;
-  static int halo() { return 16 / (int)sizeof(T); }
+  static bool tma_width_ok(int X) {
+    return kPack ? (X == 256 || X == 384 || X == 512) : (X == 128 || X == 192 || X == 256);
+  }
   static size_t tma_smem(int X, int stages) {
-    const int H = halo();
-    if (X <= 0 || stages < 2 || X % (2 * H) != 0) return 0;
+    const int H = 16 / (int)sizeof(T);
+    if (!tma_width_ok(X) || stages < 2) return 0;
     const size_t head = 128 * ((2 * (size_t)stages * 8 + 4 + 127) / 128);
     return head + (size_t)stages * L::Q * (size_t)(X + 2 * H) * sizeof(T);
   }
 
-  template <int COLL, bool FORCE>
-  static cudaError_t go_tma(const StepLaunch& s) {
+  template <int COLL, bool FORCE, int XT>
+  static cudaError_t go_tma_x(const StepLaunch& s) {
+    using Sh = TmaShape<XT, kPack>;
     TmaArgs<R> a;
     a.g = geo(s.g);
     a.c = coef_cast<R>(s.c);
@@ -188,22 +191,16 @@ struct TU {
     a.flag = s.flag;
     a.err = s.err;
     a.step = s.step;
-    a.H = halo();
-    const int Xmax = s.v.X;
-    const int ntx = (s.g.nx + Xmax - 1) / Xmax;
-    // equal tiles, each a multiple of 2H
-    int X = (s.g.nx + ntx - 1) / ntx;
-    X = (X + 2 * a.H - 1) / (2 * a.H) * (2 * a.H);
-    a.X = X;
-    a.ntx = (s.g.nx + X - 1) / X;
+    a.ntx = (s.g.nx + XT - 1) / XT;
     a.stages = s.v.stages;
-    a.slot = X + 2 * a.H;
-    a.ntiles = (long long)a.ntx * s.g.ny * s.g.nz;
+    const long long ntiles = (long long)a.ntx * s.g.ny * s.g.nz;
+    if (ntiles >= (1LL << 31)) return cudaErrorInvalidValue;
+    a.ntiles = (int)ntiles;
     a.timeout_ns = s.wait_ns > 0 ? s.wait_ns : 2000000000LL;
     a.extra_tx = s.extra_tx;
-    const size_t smem = tma_smem(X, a.stages);
+    const size_t smem = tma_smem(XT, a.stages);
     if (smem == 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = &k_step_tma<L, COLL, S, FORCE, kPack>;
+    auto kern = &k_step_tma<L, COLL, S, FORCE, kPack, XT>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -211,13 +208,37 @@ struct TU {
       attr_set = true;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long blocks = (long long)per_sm * (s.sms > 0 ? s.sms : 1);
     if (blocks > a.ntiles) blocks = a.ntiles;
-    kern<<<(unsigned)blocks, kTmaThreads, smem, s.stream>>>(a);
+    kern<<<(unsigned)blocks, Sh::kThreads, smem, s.stream>>>(a);
     return cudaGetLastError();
+  }
+
+  template <int COLL, bool FORCE>
+  static cudaError_t go_tma(const StepLaunch& s) {
+    if constexpr (kPack) {
+      switch (s.v.X) {
+        case 256:
+          return go_tma_x<COLL, FORCE, 256>(s);
+        case 384:
+          return go_tma_x<COLL, FORCE, 384>(s);
+        case 512:
+          return go_tma_x<COLL, FORCE, 512>(s);
+      }
+    } else {
+      switch (s.v.X) {
+        case 128:
+          return go_tma_x<COLL, FORCE, 128>(s);
+        case 192:
+          return go_tma_x<COLL, FORCE, 192>(s);
+        case 256:
+          return go_tma_x<COLL, FORCE, 256>(s);
+      }
+    }
+    return cudaErrorInvalidValue;
   }
 
   template <int COLL>
