@@ -83,38 +83,47 @@ struct Ar<double> {
     return (!(rho > 0.0) || !(usq <= 1.0)) ? 1u : 0u;
   }
 };
+// The two floats travel as separate 32-bit operands and are packed into the
+// 64-bit f32x2 operand inside the asm block (register-pair moves that the
+// assembler coalesces), so no value ever round-trips through local memory.
 template <>
 struct Ar<F2> {
   using S = float;
-  __device__ __forceinline__ static unsigned long long u(F2 a) {
-    unsigned long long r;
-    memcpy(&r, &a, 8);
-    return r;
-  }
-  __device__ __forceinline__ static F2 f(unsigned long long a) {
-    F2 r;
-    memcpy(&r, &a, 8);
-    return r;
-  }
   __device__ __forceinline__ static F2 add(F2 a, F2 b) {
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
-    return f(r);
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "add.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
   }
   __device__ __forceinline__ static F2 sub(F2 a, F2 b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
-    return f(r);
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
   }
   __device__ __forceinline__ static F2 mul(F2 a, F2 b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(u(a)), "l"(u(b)));
-    return f(r);
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
   }
   __device__ __forceinline__ static F2 fma(F2 a, F2 b, F2 c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(u(a)), "l"(u(b)), "l"(u(c)));
-    return f(r);
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, c, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tmov.b64 c, {%6, %7};\n\t"
+        "fma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
   }
   __device__ __forceinline__ static F2 rcp(F2 a) { return F2{__frcp_rn(a.x), __frcp_rn(a.y)}; }
   __device__ __forceinline__ static F2 c(double v) { return F2{float(v), float(v)}; }

@@ -78,14 +78,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// try_wait with a suspend-time hint: a warp whose phase is not complete sleeps
+// (up to kSuspendNs) instead of re-issuing, leaving the issue slots to others.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -106,12 +109,12 @@ __device__ __forceinline__ long long tma_now() {
 // Bounded wait.  Returns false if the wait ran out (then the abort flag and the
 // global error word are set) or another warp aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, long long timeout_ns) {
+                                          int* err, long long timeout_ns, bool heed_abort = true) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = tma_now();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
+    if (heed_abort && *abort_flag) return false;
     if (tma_now() - t0 > timeout_ns) {
       *abort_flag = 1;
       atomicExch(err, 1);
@@ -170,6 +173,39 @@ struct TileWalk {
 };
 
 template <class L>
+__device__ __forceinline__ int opp_dyn(int i) {
+  int r = 0;
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k)
+    if (k == i) r = L::opp(k);
+  return r;
+}
+
+// tma_source_row for a plane index known only at run time.
+template <class L>
+__device__ __forceinline__ void tma_source_row_dyn(const Geo& G, int i, int y, int z, int& ys,
+                                                   int& zs, bool& wall) {
+  int ey = 0, ez = 0;
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k)
+    if (k == i) {
+      ey = L::cy(k);
+      ez = L::cz(k);
+    }
+  ys = y - ey;
+  zs = z - ez;
+  wall = false;
+  if (ys < 0 || ys >= G.ny) {
+    if (G.per[1]) ys = ys < 0 ? ys + G.ny : ys - G.ny;
+    else wall = true;
+  }
+  if (zs < 0 || zs >= G.nz) {
+    if (G.per[2]) zs = zs < 0 ? zs + G.nz : zs - G.nz;
+    else wall = true;
+  }
+}
+
+template <class L>
 __device__ __forceinline__ void tma_source_row(const Geo& G, int i, int y, int z, int& ys, int& zs,
                                                bool& wall) {
   ys = y - L::cy(i);
@@ -219,15 +255,18 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane != 0) return;
+    // Lane i (< Q) copies population plane i; lane 0 sets the expected byte
+    // count.  The warp waits for the stage together, so it stays converged.
+    const unsigned full_mask = 0xffffffffu;
     TileWalk w(a.ntiles, a.ntx, G.ny);
     int k = 0;
     int s = 0;       // stage of tile k
     uint32_t u = 0;  // use count of stage s
     bool ok = true;
     for (; w.more(); w.next(), ++k) {
-      if (u > 0 && !mbar_wait(smem_addr(empty + s), (u - 1) & 1u, abort_flag, a.err,
-                               a.timeout_ns)) {
+      // every lane observes the stage's release itself before writing into it
+      if (u > 0 && !mbar_wait_warp(smem_addr(empty + s), (u - 1) & 1u, abort_flag, a.err,
+                                   a.timeout_ns)) {
         ok = false;
         break;
       }
@@ -241,26 +280,22 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
       const bool rwrap = G.per[0] && xe == G.nx;
       const uint32_t main_bytes = (uint32_t)(hi - lo) * sizeof(T);
       constexpr uint32_t halo_bytes = (uint32_t)HT * sizeof(T);
-      uint32_t total = 0;
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        int ys, zs;
-        bool wall;
-        tma_source_row<L>(G, i, y, z, ys, zs, wall);
-        total += main_bytes;
-        if (!wall) total += (lwrap ? halo_bytes : 0u) + (rwrap ? halo_bytes : 0u);
-      }
+      int ys = 0, zs = 0;
+      bool wall = false;
+      const int i = lane;
+      if (i < L::Q) tma_source_row_dyn<L>(G, i, y, z, ys, zs, wall);
+      const unsigned walls = __ballot_sync(full_mask, i < L::Q && wall);
       const uint32_t fb = smem_addr(full + s);
-      mbar_arrive_expect_tx(fb, total + (uint32_t)a.extra_tx);
-      T* st = ring + s * stage_elems;
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        int ys, zs;
-        bool wall;
-        tma_source_row<L>(G, i, y, z, ys, zs, wall);
-        T* slot = st + i * SLOT;  // slot[k] holds x = x0 - HT + k
-        const T* rowp = wall ? src + L::opp(i) * G.plane + ((long long)z * G.ny + y) * G.pitch
-                             : src + i * G.plane + ((long long)zs * G.ny + ys) * G.pitch;
+      if (lane == 0) {
+        const uint32_t nwrap = (uint32_t)(L::Q - __popc(walls)) * ((lwrap ? 1u : 0u) + (rwrap ? 1u : 0u));
+        mbar_arrive_expect_tx(fb, main_bytes * L::Q + nwrap * halo_bytes + (uint32_t)a.extra_tx);
+      }
+      __syncwarp();
+      if (i < L::Q) {
+        T* slot = ring + s * stage_elems + i * SLOT;  // slot[k] holds x = x0 - HT + k
+        const int pi = wall ? opp_dyn<L>(i) : i;
+        const long long r = wall ? ((long long)z * G.ny + y) : ((long long)zs * G.ny + ys);
+        const T* rowp = src + pi * G.plane + r * G.pitch;
         bulk_g2s(smem_addr(slot + (lo - (x0 - HT))), rowp + lo, main_bytes, fb);
         if (!wall) {
           if (lwrap) bulk_g2s(smem_addr(slot), rowp + G.nx - HT, halo_bytes, fb);
@@ -272,12 +307,11 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
         ++u;
       }
     }
-    if (!ok) {
+    if (!ok && lane == 0) {
       // let every issued copy land before the block's shared memory is released
-      for (int kk = (k > ST ? k - ST : 0); kk < k; ++kk) {
-        volatile int dummy = 0;
-        mbar_wait(smem_addr(full + kk % ST), (uint32_t)((kk / ST) & 1), &dummy, a.err, a.timeout_ns);
-      }
+      for (int kk = (k > ST ? k - ST : 0); kk < k; ++kk)
+        mbar_wait(smem_addr(full + kk % ST), (uint32_t)((kk / ST) & 1), abort_flag, a.err,
+                  a.timeout_ns, false);
     }
     return;
   }
