@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -90,23 +92,30 @@ class ClockSampler:
         self.lines = []
         self.thread = None
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start nvidia-smi and wait (up to wait_s) for its first sample, so that
+        the timed region is covered from its beginning."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < wait_s:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict | None:
+    def stop(self, t0: float | None = None, t1: float | None = None) -> dict | None:
+        """Median SM clock and the throttle reasons seen in [t0, t1] (wall clock,
+        time.perf_counter), widened by one sampling period on each side."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -118,7 +127,9 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if t0 is not None and (ts < t0 - 0.1 or ts > t1 + 0.1):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -323,6 +334,200 @@ def batched(peak: float, count: int = 256, steps: int = 500):
     return out
 
 
+PRECISION_STORAGES = ("F64", "F32", "F16", "BF16")
+
+
+def channel_relax_steps(h: int, nu: float, efolds: float = 12.0) -> int:
+    """Steps for the slowest diffusive mode of a channel of height h to decay by
+    exp(-efolds) (time constant h^2 / (pi^2 nu))."""
+    return int(math.ceil(efolds * h * h / (math.pi ** 2 * nu)))
+
+
+def precision_channel(nus=(0.1,), h: int = 64, u_c: float = 0.05, with_oracle: bool = False):
+    """Accuracy of the shifted storage formats on the force-driven D3Q19 channel
+    (halfway bounce-back walls normal to y, periodic in x and z, Lambda = 3/16,
+    body force F = 8 nu u_c / h^2), run from rest to steady state.
+
+    The flow is invariant in x and z and the update is per node, so a narrow
+    32 x h x 4 slab computes, column for column, exactly what the full
+    512 x h x 512 channel does; only throughput depends on the extent.  Each
+    storage format reports the relative L2 error of u_x against the discrete
+    analytic profile (which the FP64 update reaches to rounding at Lambda = 3/16)
+    and against the FP64 run of the same length; with ``with_oracle`` the FP64
+    CPU oracle is run on one column as well."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Lattice
+    out = []
+    exact = W.poiseuille_profile(h, u_c)
+    for nu in nus:
+        F = 8.0 * nu * u_c / (h * h)
+        T = channel_relax_steps(h, nu)
+        shape = (4, h, 32)
+        rho, u = W.channel_at_rest(shape, 3)
+        ux = {}
+        for st in PRECISION_STORAGES:
+            g = Lattice(lattice="D3Q19", nx=32, ny=h, nz=4, nu=nu, Lambda=3 / 16,
+                        collision="P_TRT", storage=st, force=(F, 0.0, 0.0), periodic=(1, 0, 1))
+            g.init_equilibrium(rho, u)
+            g.step(T)
+            _, uu = g.macros()
+            ux[st] = uu[0].double().cpu().numpy()
+            rc, _ = g.status()
+            del g
+            if rc != 0:
+                ux[st] = None
+        torch.cuda.synchronize()
+        row = {"nu": nu, "force": F, "steps": T}
+        ref = np.broadcast_to(exact[None, :, None], shape)
+        for st in PRECISION_STORAGES:
+            if ux[st] is None:
+                row[st] = {"diverged": True}
+                continue
+            row[st] = {"l2_vs_analytic": rel_l2(ux[st], ref),
+                       "l2_vs_fp64": rel_l2(ux[st], ux["F64"])}
+        if with_oracle:
+            import oracle as O
+            wp, wm = O.rates(nu=nu, Lambda=3 / 16)
+            p = O.Params(O.D3Q19, 1, h, 1, collision=O.P_TRT, omega_plus=wp, omega_minus=wm,
+                         force=(F, 0.0, 0.0), periodic=(1, 0, 1))
+            r0, u0 = W.channel_at_rest(p.shape, 3)
+            _, uo = O.macros(p, O.step(p, O.init_equilibrium(p, r0, u0), T, nthreads=1))
+            col = uo[0][:, :, 0:1]
+            row["oracle"] = {"l2_vs_analytic": rel_l2(col, exact[None, :, None]),
+                             "gpu_fp64_vs_oracle": rel_l2(ux["F64"][:, :, 0:1][0:1], col)}
+            for st in ("F32", "F16", "BF16"):
+                if ux[st] is not None:
+                    row[st]["l2_vs_oracle"] = rel_l2(ux[st][0:1, :, 0:1], col)
+        out.append(row)
+    return out
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = float(np.sqrt(np.sum(b * b)))
+    return float(np.sqrt(np.sum((a - b) ** 2)) / den) if den > 0 else float("nan")
+
+
+def precision_throughput(peak: float, nx: int = 512, h: int = 64, nz: int = 512):
+    """MLUPS of the full force-driven D3Q19 channel (nx x h x nz, walls normal to
+    y) per storage format, FP32 arithmetic, kernel-only."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Lattice
+    out = {}
+    nu, u_c = 0.1, 0.05
+    F = 8.0 * nu * u_c / (h * h)
+    for st in ("F32", "F16", "BF16"):
+        g = Lattice(lattice="D3Q19", nx=nx, ny=h, nz=nz, nu=nu, Lambda=3 / 16,
+                    collision="P_TRT", storage=st, force=(F, 0.0, 0.0), periodic=(1, 0, 1))
+        rho, u = W.channel_at_rest((nz, h, nx), 3)
+        g.init_equilibrium(rho, u)
+        g.autotune(reps=3, report=False)
+        dt = time_kernel(g, 10, 3)
+        bpn = BYTES_PER_NODE[("D3Q19", st)]
+        out[st] = {"mlups": g.N / dt / 1e6, "kernel_ms": dt * 1e3,
+                   "frac": bpn * g.N / dt / 1e9 / peak, "variant": g.variants()[g.variant]}
+        del g
+        torch.cuda.empty_cache()
+    out["f16_over_f32"] = out["F16"]["mlups"] / out["F32"]["mlups"]
+    out["workload"] = f"D3Q19 P-TRT force-driven channel {nx}x{h}x{nz}, Lambda=3/16"
+    return out
+
+
+def precision_cylinder(steps: int = 20000, nx: int = 2048, ny: int = 1024, side: int = 64,
+                       re: float = 0.1):
+    """D2Q9 creeping flow past a centred square cylinder between halfway
+    bounce-back walls (normal to y), periodic in x, driven by the body force that
+    would give an empty-channel centre-line speed u_c, Re = u_c side / nu with
+    nu = 1/6 (tau+ = 1).  Every storage format runs `steps` steps from rest; the
+    relative L2 error of the fluid velocity against the FP64 run of the same
+    length, and the MLUPS of each format, are reported."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Lattice
+    nu = 1.0 / 6.0
+    u_c = re * nu / side
+    F = 8.0 * nu * u_c / (ny * ny)
+    solid = W.square_cylinder_mask(nx, ny, side)
+    shape = (1, ny, nx)
+    rho, u = W.channel_at_rest(shape, 2)
+    vel, rates = {}, {}
+    for st in PRECISION_STORAGES:
+        g = Lattice(lattice="D2Q9", nx=nx, ny=ny, nu=nu, Lambda=3 / 16, collision="P_TRT",
+                    storage=st, force=(F, 0.0, 0.0), periodic=(1, 0, 1), solid=solid)
+        g.init_equilibrium(rho, u)
+        g.step(steps)
+        _, uu = g.macros()
+        vel[st] = uu.double().cpu().numpy()
+        dt = time_kernel(g, 10, 3)
+        rates[st] = g.N / dt / 1e6
+        del g
+        torch.cuda.empty_cache()
+    fluid = solid[0] == 0
+    out = {"workload": f"D2Q9 P-TRT square cylinder {nx}x{ny}, side {side}, Re={re}, "
+                       f"nu=1/6, Lambda=3/16, {steps} steps from rest",
+           "u_c": u_c, "force": F}
+    for st in PRECISION_STORAGES:
+        out[st] = {"mlups": rates[st],
+                   "l2_vs_fp64": rel_l2(vel[st][:, 0][:, fluid], vel["F64"][:, 0][:, fluid])}
+    return out
+
+
+def run_precision_study(args):
+    """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
+    oracle on one column for the first two), the full-channel throughput per
+    format, and the square cylinder."""
+    import torch
+    from paper_2602_06686_gb300 import build
+    build.build()
+    peak = measured_peaks()["hbm_gbs"]
+    res = {"study": "precision",
+           "channel": precision_channel((0.1, 0.01, 0.001), with_oracle=False),
+           "channel_oracle": precision_channel((0.1, 0.01), with_oracle=True),
+           "throughput": precision_throughput(peak),
+           "cylinder": precision_cylinder(args.cyl_steps)}
+    torch.cuda.synchronize()
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def run_case(args):
+    """One lattice configuration for a profiler: LATTICE:STORAGE:NX,NY,NZ[:COLLISION],
+    fixed kernel variant (by name; the default variant otherwise), ``--warmup``
+    updates then ``--inner`` updates."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import build, Lattice
+    build.build()
+    parts = args.case.split(":")
+    lat, st = parts[0], parts[1]
+    dims = [int(v) for v in parts[2].split(",")]
+    coll = parts[3] if len(parts) > 3 else "P_TRT"
+    nx, ny = dims[0], dims[1]
+    nz = dims[2] if len(dims) > 2 else 1
+    if lat == "D2Q9":
+        g = Lattice(lattice="D2Q9", nx=nx, ny=ny, nu=0.1 * nx / 1e5, tau_minus=1 / 1.6,
+                    collision=coll, storage=st)
+        rho, u = W.double_shear_rect(nx, ny)
+    else:
+        g = Lattice(lattice="D3Q19", nx=nx, ny=ny, nz=nz, nu=0.05 * nx / (2 * math.pi * 1600),
+                    Lambda=0.25, collision=coll, storage=st)
+        rho, u = W.channel_at_rest((nz, ny, nx), 3)
+        u[0] = 0.02
+    g.init_equilibrium(rho, u)
+    if args.variant:
+        g.variant = g.variants().index(args.variant)
+    g.step(args.warmup)
+    g.step(args.inner)
+    torch.cuda.synchronize()
+    rc, first = g.status()
+    print(json.dumps({"case": args.case, "variant": g.variants()[g.variant],
+                      "updates": args.warmup + args.inner, "status": rc}), flush=True)
+    return 0 if rc == 0 else 1
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -368,6 +573,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    w_start = time.perf_counter()
     t_start.record(st)
     diag = None
     for k in range(args.steps):
@@ -377,9 +583,10 @@ def run_ours(args):
         diag = g.diagnostics()  # FP64 reduction, synchronises
     t_end.record(st)
     t_end.synchronize()
+    w_end = time.perf_counter()
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(w_start, w_end)
     launches = g.launches - launches0
     rc, first = g.status()
     total_s = t_start.elapsed_time(t_end) * 1e-3
@@ -418,16 +625,27 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         del g
         torch.cuda.empty_cache()
-        extra["d3q19_f32"] = secondary("D3Q19", 384, "F32", "taylor_green_3d", peak)
-        extra["d3q19_f16"] = secondary("D3Q19", 384, "F16", "taylor_green_3d", peak)
-        extra["d3q19_bf16"] = secondary("D3Q19", 384, "BF16", "taylor_green_3d", peak)
-        extra["d2q9_f16"] = secondary("D2Q9", n, "F16", "double_shear", peak)
-        extra["d2q9_trt_rlb_f32"] = secondary("D2Q9", n, "F32", "double_shear", peak, "TRT_RLB")
-        extra["d2q9_trt_f32"] = secondary("D2Q9", n, "F32", "double_shear", peak, "TRT")
-        extra["d3q19_trt_rlb_f32"] = secondary("D3Q19", 384, "F32", "taylor_green_3d", peak,
-                                               "TRT_RLB")
-        extra["d3q19_f64"] = secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)
-        extra["batch256"] = batched(peak)
+        jobs = [
+            ("d3q19_f32", lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak)),
+            ("d3q19_f16", lambda: secondary("D3Q19", 384, "F16", "taylor_green_3d", peak)),
+            ("d3q19_bf16", lambda: secondary("D3Q19", 384, "BF16", "taylor_green_3d", peak)),
+            ("d2q9_f16", lambda: secondary("D2Q9", n, "F16", "double_shear", peak)),
+            ("d2q9_trt_rlb_f32",
+             lambda: secondary("D2Q9", n, "F32", "double_shear", peak, "TRT_RLB")),
+            ("d2q9_trt_f32", lambda: secondary("D2Q9", n, "F32", "double_shear", peak, "TRT")),
+            ("d3q19_trt_rlb_f32",
+             lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, "TRT_RLB")),
+            ("d3q19_f64", lambda: secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)),
+            ("batch256", lambda: batched(peak)),
+            ("precision", lambda: {"channel": precision_channel((0.1, 0.01)),
+                                   "throughput": precision_throughput(peak)}),
+        ]
+        for key, fn in jobs:
+            try:
+                extra[key] = fn()
+            except Exception as e:  # a failed side measurement must not lose the headline
+                extra[key] = {"error": f"{type(e).__name__}: {e}"}
+                torch.cuda.synchronize()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
@@ -465,7 +683,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
@@ -473,7 +691,18 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--study", choices=["precision"], default=None,
+                    help="run the full precision study instead of the benchmark")
+    ap.add_argument("--cyl-steps", type=int, default=20000)
+    ap.add_argument("--case", default=None,
+                    help="LATTICE:STORAGE:NX,NY,NZ[:COLLISION]: run one configuration "
+                         "(--warmup + --inner updates) for a profiler and exit")
+    ap.add_argument("--variant", default=None, help="kernel variant name for --case")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
+    if args.study == "precision":
+        return run_precision_study(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

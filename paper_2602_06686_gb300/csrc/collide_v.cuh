@@ -29,7 +29,11 @@
 //              g_e*6: rest 1, axial -2, diagonal 1
 //              g_1*2: x pair -1, z pair 1, xy diagonals 1, yz diagonals -1
 //              g_2*2: x pair 1, y pair -2, z pair 1, xy 1, yz 1, xz -2.
-//   P_G fneq = sum_k w_i G(k,i) (s_k^2 / N_k) sum_j G(k,j) fneq_j.
+//   P_G fneq = sum_k w_i G(k,i) (s_k^2 / N_k) sum_j G(k,j) fneq_j, where the
+//   ghost sums are taken over the (shifted) populations: the ghost vectors are
+//   w-orthogonal to 1 and H2, which span the symmetric part of f_eq and the
+//   shift, so sum_j G(k,j) fneq_j = sum_j G(k,j) g_j exactly.  TRT and P-TRT
+//   then finish each inversion pair in one pass; TRT-RLB forms every fneq first.
 // TRT-RLB on D3Q19: the third-order components m_ab = e_a (e_b^2 - cs^2) of the
 // same odd axis a overlap (<m_ab, m_ac>_w = -cs^6); their sum (norm 2 cs^6) and
 // difference (norm 6 cs^6) are w-orthogonal.
@@ -292,231 +296,258 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
   const V feq0 = A::mul(A::c(L::w(0)), A::fma(rho, musq15, drho));
   const V np0 = A::sub(g[0], feq0);
 
-  // ---- per pair: equilibrium parts, fneq+-, sources
-  V fs[Q], fa[Q], np[Q], nm[Q], eu[Q];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    if (!is_pair_rep<L>(i)) continue;
-    const int w36 = L::w36(i);
-    eu[i] = edot<L, V>(i, u);
-    const V q = A::mul(eu[i], eu[i]);
-    const V t = A::fma(A::c(4.5), q, musq15);
-    const V t2 = A::fma(A::c(4.5), q, k3);
-    const V wr = w36 == 1 ? rho36 : A::mul(rho36, A::c(double(w36)));
-    const V wd = w36 == 1 ? drho36 : A::mul(drho36, A::c(double(w36)));
-    fs[i] = A::fma(wr, t, wd);                  // symmetric part of the shifted f_eq
-    fa[i] = A::mul(A::mul(wr, eu[i]), t2);      // antisymmetric part
-    np[i] = A::sub(A::mul(A::c(0.5), s[i]), fs[i]);
-    nm[i] = A::sub(A::mul(A::c(0.5), d[i]), fa[i]);
-  }
-
-  // ---- symmetric relaxation target R2
-  V r2[Q];
-  V r20;
-  if constexpr (COLL == C_TRT) {
-    r20 = np0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-      if (is_pair_rep<L>(i)) r2[i] = np[i];
-  } else if constexpr (COLL == C_P_TRT) {
+  if constexpr (COLL != C_TRT_RLB) {
+    // TRT and P-TRT need no moment of fneq but the ghost moments, so each pair
+    // is finished in one pass (few values live at once).  The ghost moments
+    // are taken from the populations: the ghost vectors are w-orthogonal to
+    // span{1, H2} (Eq. S_decomp), which holds the symmetric part of f_eq and
+    // the shift w_i rho0, so sum_j G(k,j) fneq_j = sum_j G(k,j) g_j exactly
+    // (up to rounding), with g_i + g_ibar = s_i.
     using Gh = GhostT<L>;
-    V m[Gh::NG];
+    constexpr int NG = COLL == C_P_TRT ? Gh::NG : 1;
+    V m[NG];
+    V r20 = np0;
+    if constexpr (COLL == C_P_TRT) {
 #pragma unroll
-    for (int k = 0; k < Gh::NG; ++k) {
-      // sum_j G(k,j) fneq_j with fneq_i + fneq_ibar = 2 np_i
-      V acc = Gh::G(k, 0) == 0 ? A::c(0.0) : A::mul(A::c(double(Gh::G(k, 0))), np0);
-      bool init = Gh::G(k, 0) != 0;
+      for (int k = 0; k < NG; ++k) {
+        V acc = Gh::G(k, 0) == 0 ? A::c(0.0) : A::mul(A::c(double(Gh::G(k, 0))), g[0]);
+        bool init = Gh::G(k, 0) != 0;
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        if (!is_pair_rep<L>(i) || Gh::G(k, i) == 0) continue;
-        acc = init ? A::fma(A::c(double(2 * Gh::G(k, i))), np[i], acc)
-                   : A::mul(A::c(double(2 * Gh::G(k, i))), np[i]);
-        init = true;
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i) || Gh::G(k, i) == 0) continue;
+          acc = init ? A::fma(A::c(double(Gh::G(k, i))), s[i], acc)
+                     : A::mul(A::c(double(Gh::G(k, i))), s[i]);
+          init = true;
+        }
+        m[k] = acc;
       }
-      m[k] = acc;
-    }
-    // R2_i = np_i - sum_k w_i G(k,i) (s_k^2/N_k) m_k as one fma chain from np_i (no
-    // product feeds a separate subtraction, so there is nothing left to contract)
-    r20 = np0;
+      // R2_i = np_i - sum_k w_i G(k,i) (s_k^2/N_k) m_k as one fma chain from np_i
 #pragma unroll
-    for (int k = 0; k < Gh::NG; ++k) {
-      if (Gh::G(k, 0) == 0) continue;
-      r20 = A::fma(A::c(-L::w(0) * Gh::G(k, 0) * Gh::coef(k)), m[k], r20);
+      for (int k = 0; k < NG; ++k) {
+        if (Gh::G(k, 0) == 0) continue;
+        r20 = A::fma(A::c(-L::w(0) * Gh::G(k, 0) * Gh::coef(k)), m[k], r20);
+      }
     }
+    // rest: f*_0 = f_eq0 + (1 - w+) R2_0 + S+_0, S+_0 = hg w0 (-3 u.F)
+    V g0 = A::fma(A::c(c.cp), r20, feq0);
+    if (FORCE) g0 = A::fma(A::c(c.fu[0]), uF, g0);
+    g[0] = g0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (!is_pair_rep<L>(i)) continue;
-      V r = np[i];
+      const int w36 = L::w36(i);
+      const V eu = edot<L, V>(i, u);
+      const V q = A::mul(eu, eu);
+      const V t = A::fma(A::c(4.5), q, musq15);
+      const V t2 = A::fma(A::c(4.5), q, k3);
+      const V wr = w36 == 1 ? rho36 : A::mul(rho36, A::c(double(w36)));
+      const V wd = w36 == 1 ? drho36 : A::mul(drho36, A::c(double(w36)));
+      const V fs = A::fma(wr, t, wd);              // symmetric part of the shifted f_eq
+      const V fa = A::mul(A::mul(wr, eu), t2);     // antisymmetric part
+      V r2 = A::sub(A::mul(A::c(0.5), s[i]), fs);  // fneq+
+      if constexpr (COLL == C_P_TRT) {
 #pragma unroll
-      for (int k = 0; k < Gh::NG; ++k) {
-        if (Gh::G(k, i) == 0) continue;
-        r = A::fma(A::c(-L::w(i) * Gh::G(k, i) * Gh::coef(k)), m[k], r);
+        for (int k = 0; k < NG; ++k) {
+          if (Gh::G(k, i) == 0) continue;
+          r2 = A::fma(A::c(-L::w(i) * Gh::G(k, i) * Gh::coef(k)), m[k], r2);
+        }
       }
-      r2[i] = r;
+      const V nm = A::sub(A::mul(A::c(0.5), d[i]), fa);  // fneq-
+      V sym = A::fma(A::c(c.cp), r2, fs);
+      V anti = A::fma(A::c(c.cm), nm, fa);
+      if (FORCE) {
+        // S+_i = hg w (9 eu eF - 3 u.F); antisymmetric force F_i/2 + (1 - w-) F_i/2
+        sym = A::fma(A::c(c.fe[i]), eu, sym);
+        sym = A::fma(A::c(c.fu[i]), uF, sym);
+        anti = A::add(anti, A::c(c.fa[i]));
+      }
+      g[i] = A::add(sym, anti);
+      g[L::opp(i)] = A::sub(sym, anti);
     }
+    return badmask;
   } else {
-    // TRT-RLB: w-orthogonal projection onto span{H2}:
-    // A2_ab = sum_i (e_a e_b - cs^2 d_ab) fneq_i; R2_i = 4.5 w_i [sum_a H2_i,aa A_aa + 2 sum_{a<b} e_a e_b A_ab]
-    V Ad[3], Ao[3];  // diagonal xx, yy, zz and off-diagonal xy, xz, yz
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Ad[a] = A::mul(A::c(-1.0 / 3.0), np0);
-      Ao[a] = A::c(0.0);
-    }
-    bool oinit[3] = {false, false, false};
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      if (!is_pair_rep<L>(i)) continue;
-#pragma unroll
-      for (int a = 0; a < L::D; ++a) {
-        const int e = ecomp<L>(i, a);
-        Ad[a] = A::fma(A::c(2.0 * (e * e - 1.0 / 3.0)), np[i], Ad[a]);
-      }
-#pragma unroll
-      for (int o = 0; o < 3; ++o) {
-        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
-        if (b >= L::D) continue;
-        const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
-        if (eab == 0) continue;
-        Ao[o] = oinit[o] ? A::fma(A::c(2.0 * eab), np[i], Ao[o]) : A::mul(A::c(2.0 * eab), np[i]);
-        oinit[o] = true;
-      }
-    }
-    V tr = A::add(Ad[0], Ad[1]);
-    if (L::D == 3) tr = A::add(tr, Ad[2]);
-    r20 = A::mul(A::c(4.5 * L::w(0) * (-1.0 / 3.0)), tr);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      if (!is_pair_rep<L>(i)) continue;
-      V h = A::mul(A::c(ecomp<L>(i, 0) * ecomp<L>(i, 0) - 1.0 / 3.0), Ad[0]);
-#pragma unroll
-      for (int a = 1; a < L::D; ++a) {
-        const int e = ecomp<L>(i, a);
-        h = A::fma(A::c(e * e - 1.0 / 3.0), Ad[a], h);
-      }
-#pragma unroll
-      for (int o = 0; o < 3; ++o) {
-        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
-        if (b >= L::D) continue;
-        const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
-        if (eab != 0) h = A::fma(A::c(2.0 * eab), Ao[o], h);
-      }
-      r2[i] = A::mul(A::c(4.5 * L::w(i)), h);
-    }
-  }
 
-  // ---- antisymmetric relaxation target R3 and post-collision
-  V r3[Q];
-  if constexpr (COLL == C_TRT_RLB) {
-    // fneq_i - fneq_ibar = 2 nm_i; modes m_ab = e_a (e_b^2 - cs^2)
-    auto mode = [](int a, int b, int i) constexpr -> double {
-      const int ea = ecomp<L>(i, a), eb = ecomp<L>(i, b);
-      return ea * (eb * eb - 1.0 / 3.0);
-    };
-    if constexpr (L::D == 2) {
-      V Axyy = A::c(0.0), Axxy = A::c(0.0);
-      bool i1 = false, i2 = false;
+    // ---- TRT-RLB: the Hermite projections need every fneq first.
+    // per pair: equilibrium parts, fneq+-
+    V fs[Q], fa[Q], np[Q], nm[Q];
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        if (!is_pair_rep<L>(i)) continue;
-        if (mode(0, 1, i) != 0.0) {
-          Axyy = i1 ? A::fma(A::c(2.0 * mode(0, 1, i)), nm[i], Axyy) : A::mul(A::c(2.0 * mode(0, 1, i)), nm[i]);
-          i1 = true;
-        }
-        if (mode(1, 0, i) != 0.0) {
-          Axxy = i2 ? A::fma(A::c(2.0 * mode(1, 0, i)), nm[i], Axxy) : A::mul(A::c(2.0 * mode(1, 0, i)), nm[i]);
-          i2 = true;
-        }
-      }
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        if (!is_pair_rep<L>(i)) continue;
-        V h = A::c(0.0);
-        bool hi = false;
-        if (mode(0, 1, i) != 0.0) {
-          h = A::mul(A::c(13.5 * L::w(i) * mode(0, 1, i)), Axyy);
-          hi = true;
-        }
-        if (mode(1, 0, i) != 0.0)
-          h = hi ? A::fma(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy, h)
-                 : A::mul(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy);
-        r3[i] = h;
-      }
-    } else {
-      V As[3], Adf[3];
-      bool is[3] = {false, false, false}, id[3] = {false, false, false};
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      const int w36 = L::w36(i);
+      const V eu = edot<L, V>(i, u);
+      const V q = A::mul(eu, eu);
+      const V t = A::fma(A::c(4.5), q, musq15);
+      const V t2 = A::fma(A::c(4.5), q, k3);
+      const V wr = w36 == 1 ? rho36 : A::mul(rho36, A::c(double(w36)));
+      const V wd = w36 == 1 ? drho36 : A::mul(drho36, A::c(double(w36)));
+      fs[i] = A::fma(wr, t, wd);
+      fa[i] = A::mul(A::mul(wr, eu), t2);
+      np[i] = A::sub(A::mul(A::c(0.5), s[i]), fs[i]);
+      nm[i] = A::sub(A::mul(A::c(0.5), d[i]), fa[i]);
+    }
+
+    // ---- symmetric relaxation target R2
+    V r2[Q];
+    V r20;
+    {
+      // TRT-RLB: w-orthogonal projection onto span{H2}:
+      // A2_ab = sum_i (e_a e_b - cs^2 d_ab) fneq_i; R2_i = 4.5 w_i [sum_a H2_i,aa A_aa + 2 sum_{a<b} e_a e_b A_ab]
+      V Ad[3], Ao[3];  // diagonal xx, yy, zz and off-diagonal xy, xz, yz
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        As[a] = A::c(0.0);
-        Adf[a] = A::c(0.0);
+        Ad[a] = A::mul(A::c(-1.0 / 3.0), np0);
+        Ao[a] = A::c(0.0);
       }
+      bool oinit[3] = {false, false, false};
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         if (!is_pair_rep<L>(i)) continue;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
-          const double sv = mode(a, b, i) + mode(a, cc, i);
-          const double dv = mode(a, b, i) - mode(a, cc, i);
-          if (sv != 0.0) {
-            As[a] = is[a] ? A::fma(A::c(2.0 * sv), nm[i], As[a]) : A::mul(A::c(2.0 * sv), nm[i]);
-            is[a] = true;
-          }
-          if (dv != 0.0) {
-            Adf[a] = id[a] ? A::fma(A::c(2.0 * dv), nm[i], Adf[a]) : A::mul(A::c(2.0 * dv), nm[i]);
-            id[a] = true;
-          }
+        for (int a = 0; a < L::D; ++a) {
+          const int e = ecomp<L>(i, a);
+          Ad[a] = A::fma(A::c(2.0 * (e * e - 1.0 / 3.0)), np[i], Ad[a]);
+        }
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+          if (b >= L::D) continue;
+          const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+          if (eab == 0) continue;
+          Ao[o] = oinit[o] ? A::fma(A::c(2.0 * eab), np[i], Ao[o]) : A::mul(A::c(2.0 * eab), np[i]);
+          oinit[o] = true;
         }
       }
+      V tr = A::add(Ad[0], Ad[1]);
+      if (L::D == 3) tr = A::add(tr, Ad[2]);
+      r20 = A::mul(A::c(4.5 * L::w(0) * (-1.0 / 3.0)), tr);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         if (!is_pair_rep<L>(i)) continue;
-        V h = A::c(0.0);
-        bool hi = false;
+        V h = A::mul(A::c(ecomp<L>(i, 0) * ecomp<L>(i, 0) - 1.0 / 3.0), Ad[0]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
-          const double sv = mode(a, b, i) + mode(a, cc, i);
-          const double dv = mode(a, b, i) - mode(a, cc, i);
-          if (sv != 0.0) {
-            h = hi ? A::fma(A::c(13.5 * L::w(i) * sv), As[a], h) : A::mul(A::c(13.5 * L::w(i) * sv), As[a]);
-            hi = true;
-          }
-          if (dv != 0.0) {
-            h = hi ? A::fma(A::c(4.5 * L::w(i) * dv), Adf[a], h) : A::mul(A::c(4.5 * L::w(i) * dv), Adf[a]);
-            hi = true;
-          }
+        for (int a = 1; a < L::D; ++a) {
+          const int e = ecomp<L>(i, a);
+          h = A::fma(A::c(e * e - 1.0 / 3.0), Ad[a], h);
         }
-        r3[i] = h;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+          if (b >= L::D) continue;
+          const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+          if (eab != 0) h = A::fma(A::c(2.0 * eab), Ao[o], h);
+        }
+        r2[i] = A::mul(A::c(4.5 * L::w(i)), h);
       }
     }
-  }
 
-  // rest: f*_0 = f_eq0 + (1 - w+) R2_0 + S+_0, S+_0 = hg w0 (-3 u.F)
-  V g0 = A::fma(A::c(c.cp), r20, feq0);
-  if (FORCE) g0 = A::fma(A::c(c.fu[0]), uF, g0);
-  g[0] = g0;
+    // ---- antisymmetric relaxation target R3 and post-collision
+    V r3[Q];
+    {
+      // fneq_i - fneq_ibar = 2 nm_i; modes m_ab = e_a (e_b^2 - cs^2)
+      auto mode = [](int a, int b, int i) constexpr -> double {
+        const int ea = ecomp<L>(i, a), eb = ecomp<L>(i, b);
+        return ea * (eb * eb - 1.0 / 3.0);
+      };
+      if constexpr (L::D == 2) {
+        V Axyy = A::c(0.0), Axxy = A::c(0.0);
+        bool i1 = false, i2 = false;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    if (!is_pair_rep<L>(i)) continue;
-    V sym = A::fma(A::c(c.cp), r2[i], fs[i]);
-    V anti;
-    if constexpr (COLL == C_TRT_RLB) {
-      anti = A::fma(A::c(c.cm), r3[i], fa[i]);
-    } else {
-      anti = A::fma(A::c(c.cm), nm[i], fa[i]);
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i)) continue;
+          if (mode(0, 1, i) != 0.0) {
+            Axyy = i1 ? A::fma(A::c(2.0 * mode(0, 1, i)), nm[i], Axyy) : A::mul(A::c(2.0 * mode(0, 1, i)), nm[i]);
+            i1 = true;
+          }
+          if (mode(1, 0, i) != 0.0) {
+            Axxy = i2 ? A::fma(A::c(2.0 * mode(1, 0, i)), nm[i], Axxy) : A::mul(A::c(2.0 * mode(1, 0, i)), nm[i]);
+            i2 = true;
+          }
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i)) continue;
+          V h = A::c(0.0);
+          bool hi = false;
+          if (mode(0, 1, i) != 0.0) {
+            h = A::mul(A::c(13.5 * L::w(i) * mode(0, 1, i)), Axyy);
+            hi = true;
+          }
+          if (mode(1, 0, i) != 0.0)
+            h = hi ? A::fma(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy, h)
+                   : A::mul(A::c(13.5 * L::w(i) * mode(1, 0, i)), Axxy);
+          r3[i] = h;
+        }
+      } else {
+        V As[3], Adf[3];
+        bool is[3] = {false, false, false}, id[3] = {false, false, false};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          As[a] = A::c(0.0);
+          Adf[a] = A::c(0.0);
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i)) continue;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+            const double sv = mode(a, b, i) + mode(a, cc, i);
+            const double dv = mode(a, b, i) - mode(a, cc, i);
+            if (sv != 0.0) {
+              As[a] = is[a] ? A::fma(A::c(2.0 * sv), nm[i], As[a]) : A::mul(A::c(2.0 * sv), nm[i]);
+              is[a] = true;
+            }
+            if (dv != 0.0) {
+              Adf[a] = id[a] ? A::fma(A::c(2.0 * dv), nm[i], Adf[a]) : A::mul(A::c(2.0 * dv), nm[i]);
+              id[a] = true;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i)) continue;
+          V h = A::c(0.0);
+          bool hi = false;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+            const double sv = mode(a, b, i) + mode(a, cc, i);
+            const double dv = mode(a, b, i) - mode(a, cc, i);
+            if (sv != 0.0) {
+              h = hi ? A::fma(A::c(13.5 * L::w(i) * sv), As[a], h) : A::mul(A::c(13.5 * L::w(i) * sv), As[a]);
+              hi = true;
+            }
+            if (dv != 0.0) {
+              h = hi ? A::fma(A::c(4.5 * L::w(i) * dv), Adf[a], h) : A::mul(A::c(4.5 * L::w(i) * dv), Adf[a]);
+              hi = true;
+            }
+          }
+          r3[i] = h;
+        }
+      }
     }
-    if (FORCE) {
-      // S+_i = hg w (9 eu eF - 3 u.F); antisymmetric force: F_i/2 + (1 - w-) F_i/2
-      // (P-TRT, TRT) or F_i/2 (TRT-RLB, whose R3 already carries the first-order part)
-      sym = A::fma(A::c(c.fe[i]), eu[i], sym);
-      sym = A::fma(A::c(c.fu[i]), uF, sym);
-      anti = A::add(anti, A::c(c.fa[i]));
+
+    // rest: f*_0 = f_eq0 + (1 - w+) R2_0 + S+_0, S+_0 = hg w0 (-3 u.F)
+    V g0 = A::fma(A::c(c.cp), r20, feq0);
+    if (FORCE) g0 = A::fma(A::c(c.fu[0]), uF, g0);
+    g[0] = g0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!is_pair_rep<L>(i)) continue;
+      V sym = A::fma(A::c(c.cp), r2[i], fs[i]);
+      V anti = A::fma(A::c(c.cm), r3[i], fa[i]);
+      if (FORCE) {
+        // S+_i = hg w (9 eu eF - 3 u.F); antisymmetric force F_i/2 (R3 already
+        // carries the first-order part)
+        sym = A::fma(A::c(c.fe[i]), edot<L, V>(i, u), sym);
+        sym = A::fma(A::c(c.fu[i]), uF, sym);
+        anti = A::add(anti, A::c(c.fa[i]));
+      }
+      g[i] = A::add(sym, anti);
+      g[L::opp(i)] = A::sub(sym, anti);
     }
-    g[i] = A::add(sym, anti);
-    g[L::opp(i)] = A::sub(sym, anti);
+    return badmask;
   }
-  return badmask;
 }
 
 }  // namespace lbm

@@ -37,6 +37,20 @@ struct StF16 {
   static constexpr int VBYTES = 16;
   __device__ __forceinline__ static R dec(T v) { return __half2float(v); }
   __device__ __forceinline__ static T enc(R v) { return __float2half_rn(v); }
+  // two adjacent elements as one 32-bit word (element a in the low half)
+  __device__ __forceinline__ static void dec2(uint32_t w, R& a, R& b) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    const float2 f = __half22float2(h);
+    a = f.x;
+    b = f.y;
+  }
+  __device__ __forceinline__ static uint32_t enc2(R a, R b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    uint32_t w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
 };
 struct StBF16 {
   using T = __nv_bfloat16;
@@ -45,6 +59,19 @@ struct StBF16 {
   static constexpr int VBYTES = 16;
   __device__ __forceinline__ static R dec(T v) { return __bfloat162float(v); }
   __device__ __forceinline__ static T enc(R v) { return __float2bfloat16_rn(v); }
+  __device__ __forceinline__ static void dec2(uint32_t w, R& a, R& b) {
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    const float2 f = __bfloat1622float2(h);
+    a = f.x;
+    b = f.y;
+  }
+  __device__ __forceinline__ static uint32_t enc2(R a, R b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
 };
 
 template <int BYTES>

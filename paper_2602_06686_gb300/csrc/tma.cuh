@@ -318,10 +318,15 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
 
   // -------------------------------------------------------------- consumers
   constexpr int NPT = Sh::kNPT;
+  // 16-bit storage: a thread's node pair is adjacent (x0 + 2j, x0 + 2j + 1), so
+  // unshifted planes load, and every plane stores, one 32-bit word per pair.
+  // 32-bit storage keeps the split pair (x0 + j, x0 + j + X/2), whose scalar
+  // shared reads are free of bank conflicts for every x shift.
+  constexpr bool ADJ = PACK && sizeof(T) == 2;
   const int ct = threadIdx.x - 32;  // 0 .. kConsumers-1: this thread's node (pair)
   int jn[NPT];
-  jn[0] = ct;
-  if (PACK) jn[NPT - 1] = ct + XT / 2;
+  jn[0] = ADJ ? 2 * ct : ct;
+  if (PACK) jn[NPT - 1] = ADJ ? 2 * ct + 1 : ct + XT / 2;
   TileWalk w(a.ntiles, a.ntx, G.ny);
   int s = 0;
   uint32_t u = 0;
@@ -346,7 +351,16 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const T* slot = st + i * SLOT + HT - L::cx(i);
-        if constexpr (PACK) {
+        if constexpr (ADJ) {
+          if (L::cx(i) == 0) {
+            // slot + HT is 16-byte aligned and jn[0] even: one aligned word
+            float a0, a1;
+            S::dec2(*reinterpret_cast<const uint32_t*>(slot + jn[0]), a0, a1);
+            g[i] = F2{a0, a1};
+          } else {
+            g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[NPT - 1]])};
+          }
+        } else if constexpr (PACK) {
           g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[NPT - 1]])};
         } else {
           g[i] = S::dec(slot[jn[0]]);
@@ -393,7 +407,14 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
     T* op = dst + own + x0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      if constexpr (PACK) {
+      if constexpr (ADJ) {
+        // op + jn[0] is 4-byte aligned (16-byte row pitch, even x0 + jn[0])
+        if (act[NPT - 1]) {
+          *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(g[i].x, g[i].y);
+        } else if (act[0]) {
+          op[jn[0]] = S::enc(g[i].x);
+        }
+      } else if constexpr (PACK) {
         if (act[0]) op[jn[0]] = S::enc(g[i].x);
         if (act[NPT - 1]) op[jn[NPT - 1]] = S::enc(g[i].y);
       } else {

@@ -59,6 +59,26 @@ def test_ghost_moments_vanish_after_ptrt(lat):
     assert np.max(np.abs(g_t)) > 1e-4 * np.max(np.abs(g_pre))
 
 
+@pytest.mark.parametrize("lat", LATTICES)
+def test_equilibrium_and_rest_weights_have_no_ghost_content(lat):
+    """The ghost vectors are w-orthogonal to span{1, H2} (Eq. S_decomp), which
+    holds the rest weights and the symmetric part of the third-order f_eq (Eq.
+    feq), so the ghost moments of f_eq(rho, u) vanish for any rho, u and those of
+    f_neq equal those of f (up to rounding).  Negative control: the ghost moments
+    of a random state do not vanish."""
+    info = O.lattice_info(lat)
+    phi, w = info["phi"], info["w"]
+    assert np.max(np.abs(phi @ w)) < 1e-15
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        rho = 1.0 + 0.2 * rng.uniform(-1, 1)
+        u = 0.15 * rng.uniform(-1, 1, size=info["D"])
+        feq = O.equilibrium(lat, rho, u)
+        assert np.max(np.abs(phi @ feq)) < 1e-15
+    _, f = _states(lat, 5, 32)
+    assert np.min(np.max(np.abs(f @ phi.T), axis=1)) > 1e-6
+
+
 def test_d2q9_ghost_vanishes_with_printed_mode(golden):
     """Same as above with the printed D2Q9 mode values (App. A.1), not the oracle's."""
     rows = golden("d2q9_ghost.txt")
