@@ -271,6 +271,36 @@ def time_kernel(lat_obj, inner: int, reps: int):
     return e0.elapsed_time(e1) / (reps * inner) * 1e-3
 
 
+def copy_ceiling_at(nbytes: int, reps: int = 20) -> dict:
+    """Copy bandwidth (read + write bytes / time) at one population buffer's size:
+    the library's 128-bit copy kernel and torch's copy_, CUDA events, best of
+    `reps` after warm-up."""
+    import torch
+    from paper_2602_06686_gb300 import copy_ceiling
+    n = (nbytes // 16) * 16
+    a = torch.empty(n, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    st = torch.cuda.current_stream()
+    out = {"bytes": n}
+    for name, fn in (("lbm_copy", lambda: copy_ceiling(a, b, n, st)),
+                     ("torch_copy", lambda: b.copy_(a))):
+        for _ in range(3):
+            fn()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        out[name + "_gbs"] = 2 * n / best / 1e9
+    del a, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision="P_TRT"):
     """MLUPS and roofline fraction of another workload (kernel-only, few steps)."""
     import torch
@@ -289,6 +319,9 @@ def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision=
     out["diverged"] = rc != 0
     del g
     torch.cuda.empty_cache()
+    cc = copy_ceiling_at(bpn * N // 2)
+    out["copy_ceiling_gbs"] = max(cc["lbm_copy_gbs"], cc["torch_copy_gbs"])
+    out["frac_of_copy_ceiling"] = out["achieved_gbs"] / out["copy_ceiling_gbs"]
     return out
 
 
@@ -337,7 +370,7 @@ def batched(peak: float, count: int = 256, steps: int = 500):
 PRECISION_STORAGES = ("F64", "F32", "F16", "BF16")
 
 
-def channel_relax_steps(h: int, nu: float, efolds: float = 12.0) -> int:
+def channel_relax_steps(h: int, nu: float, efolds: float = 30.0) -> int:
     """Steps for the slowest diffusive mode of a channel of height h to decay by
     exp(-efolds) (time constant h^2 / (pi^2 nu))."""
     return int(math.ceil(efolds * h * h / (math.pi ** 2 * nu)))
@@ -436,56 +469,65 @@ def precision_throughput(peak: float, nx: int = 512, h: int = 64, nz: int = 512)
     return out
 
 
-def precision_cylinder(steps: int = 20000, nx: int = 2048, ny: int = 1024, side: int = 64,
-                       re: float = 0.1):
-    """D2Q9 creeping flow past a centred square cylinder between halfway
-    bounce-back walls (normal to y), periodic in x, driven by the body force that
-    would give an empty-channel centre-line speed u_c, Re = u_c side / nu with
-    nu = 1/6 (tau+ = 1).  Every storage format runs `steps` steps from rest; the
-    relative L2 error of the fluid velocity against the FP64 run of the same
-    length, and the MLUPS of each format, are reported."""
+def precision_cylinder(steps: int = 0, nx: int = 2048, ny: int = 1024, side: int = 64,
+                       re: float = 0.1, ma: float = 0.1, cdmu: float = 8.252):
+    """D2Q9 creeping flow through a periodic array of square cylinders: a centred
+    side x side halfway bounce-back square in a fully periodic nx x ny lattice,
+    Ma = u0 / cs = 0.1 and Re = u0 side / nu = 0.1 (so nu = u0 side / Re and
+    tau+ = 1/2 + 3 nu, about 111), Lambda = 3/16, driven by a uniform body force
+    sized from the Stokes drag F_x = Cd,mu rho u0 nu / 2 with the paper's
+    Cd,mu = 8.252, spread over the fluid nodes.  Every storage format runs
+    `steps` steps from rest (default: 30 e-folds of the slowest diffusive mode,
+    ny^2 / (pi^2 nu) steps each); reported are the relative L2 error of the fluid
+    velocity against the FP64 run of the same length, the Reynolds number that
+    run reaches (mean fluid u_x), and the MLUPS of each format."""
     import torch
     import workloads as W
     from paper_2602_06686_gb300 import Lattice
-    nu = 1.0 / 6.0
-    u_c = re * nu / side
-    F = 8.0 * nu * u_c / (ny * ny)
+    u0 = ma / math.sqrt(3.0)
+    nu = u0 * side / re
     solid = W.square_cylinder_mask(nx, ny, side)
+    fluid = solid[0] == 0
+    F = cdmu * u0 * nu / 2.0 / float(fluid.sum())
+    if steps <= 0:
+        steps = int(math.ceil(30.0 * ny * ny / (math.pi ** 2 * nu)))
     shape = (1, ny, nx)
     rho, u = W.channel_at_rest(shape, 2)
     vel, rates = {}, {}
     for st in PRECISION_STORAGES:
         g = Lattice(lattice="D2Q9", nx=nx, ny=ny, nu=nu, Lambda=3 / 16, collision="P_TRT",
-                    storage=st, force=(F, 0.0, 0.0), periodic=(1, 0, 1), solid=solid)
+                    storage=st, force=(F, 0.0, 0.0), periodic=(1, 1, 1), solid=solid)
         g.init_equilibrium(rho, u)
         g.step(steps)
         _, uu = g.macros()
         vel[st] = uu.double().cpu().numpy()
+        rc, _ = g.status()
         dt = time_kernel(g, 10, 3)
-        rates[st] = g.N / dt / 1e6
+        rates[st] = {"mlups": g.N / dt / 1e6, "diverged": rc != 0}
         del g
         torch.cuda.empty_cache()
-    fluid = solid[0] == 0
-    out = {"workload": f"D2Q9 P-TRT square cylinder {nx}x{ny}, side {side}, Re={re}, "
-                       f"nu=1/6, Lambda=3/16, {steps} steps from rest",
-           "u_c": u_c, "force": F}
+    ux64 = vel["F64"][0, 0][fluid]
+    out = {"workload": f"D2Q9 P-TRT periodic square-cylinder array {nx}x{ny}, side {side}, "
+                       f"Ma={ma}, Re={re} (nu={nu:.4g}, tau+={0.5 + 3 * nu:.4g}), "
+                       f"Lambda=3/16, {steps} steps from rest",
+           "force": F, "re_reached_fp64": float(ux64.mean()) * side / nu}
     for st in PRECISION_STORAGES:
-        out[st] = {"mlups": rates[st],
-                   "l2_vs_fp64": rel_l2(vel[st][:, 0][:, fluid], vel["F64"][:, 0][:, fluid])}
+        out[st] = dict(rates[st])
+        out[st]["l2_vs_fp64"] = rel_l2(vel[st][:, 0][:, fluid], vel["F64"][:, 0][:, fluid])
     return out
 
 
 def run_precision_study(args):
     """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
-    oracle on one column for the first two), the full-channel throughput per
-    format, and the square cylinder."""
+    oracle on one column at nu = 0.1), the full-channel throughput per format,
+    and the square cylinder."""
     import torch
     from paper_2602_06686_gb300 import build
     build.build()
     peak = measured_peaks()["hbm_gbs"]
     res = {"study": "precision",
            "channel": precision_channel((0.1, 0.01, 0.001), with_oracle=False),
-           "channel_oracle": precision_channel((0.1, 0.01), with_oracle=True),
+           "channel_oracle": precision_channel((0.1,), with_oracle=True),
            "throughput": precision_throughput(peak),
            "cylinder": precision_cylinder(args.cyl_steps)}
     torch.cuda.synchronize()
@@ -621,6 +663,7 @@ def run_ours(args):
     bpn = BYTES_PER_NODE[("D2Q9", "F32")]
     achieved = bpn * N / kernel_s / 1e9
     khash = csrc_hash()
+    ceiling = copy_ceiling_at(bpn * N // 2) if rank == 0 else None
     extra = {}
     if rank == 0 and not args.no_extra:
         del g
@@ -637,7 +680,7 @@ def run_ours(args):
              lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, "TRT_RLB")),
             ("d3q19_f64", lambda: secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)),
             ("batch256", lambda: batched(peak)),
-            ("precision", lambda: {"channel": precision_channel((0.1, 0.01)),
+            ("precision", lambda: {"channel": precision_channel((0.1,)),
                                    "throughput": precision_throughput(peak)}),
         ]
         for key, fn in jobs:
@@ -665,7 +708,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profile_traffic(khash),
                      "peak_source": peaks["source"], "bytes_per_node": bpn,
-                     "kernel_ms": kernel_s * 1e3},
+                     "kernel_ms": kernel_s * 1e3, "copy_ceiling": ceiling,
+                     "frac_of_copy_ceiling": (achieved / max(ceiling["lbm_copy_gbs"],
+                                                             ceiling["torch_copy_gbs"])
+                                              if ceiling else None)},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -693,7 +739,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--study", choices=["precision"], default=None,
                     help="run the full precision study instead of the benchmark")
-    ap.add_argument("--cyl-steps", type=int, default=20000)
+    ap.add_argument("--cyl-steps", type=int, default=0,
+                    help="square-cylinder steps (0: 30 diffusive e-folds)")
     ap.add_argument("--case", default=None,
                     help="LATTICE:STORAGE:NX,NY,NZ[:COLLISION]: run one configuration "
                          "(--warmup + --inner updates) for a profiler and exit")
