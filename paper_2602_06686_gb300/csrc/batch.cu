@@ -32,8 +32,26 @@ struct BatchPlan {
   size_t max_tiles = 0;
 };
 
+// Register-kernel tile shapes (threads x rows); the pipelined variants follow.
 const int kShapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
 constexpr int kNumShapes = 7;
+const int kTmaWidths[] = {128, 256};
+const int kTmaDepths[] = {2, 3, 4};
+
+struct BVariant {
+  int kind;  // 0: register tiles (k_batch), 1: bulk-copy pipeline (k_batch_tma)
+  int bx, by;
+  int X, stages;
+};
+
+std::vector<BVariant> batch_variants(const Ops* ops) {
+  std::vector<BVariant> v;
+  if (ops->batch_tma)
+    for (int X : kTmaWidths)
+      for (int d : kTmaDepths) v.push_back(BVariant{1, 0, 0, X, d});
+  for (int k = 0; k < kNumShapes; ++k) v.push_back(BVariant{0, kShapes[k][0], kShapes[k][1], 0, 0});
+  return v;
+}
 
 size_t tiles_for(const Plan& p, int bx, int by) {
   return (size_t)((p.p.nx + bx - 1) / bx) * ((p.p.ny + by - 1) / by) * p.p.nz;
@@ -85,7 +103,10 @@ struct lbm_batch {
   bool bound = false;
   int cur = 0;          // 0: state in A, 1: state in B
   long long t = 0;      // completed steps
-  int shape = 0;        // tile shape index
+  int shape = 0;        // variant index into vars
+  std::vector<BVariant> vars;
+  std::vector<BatchDesc> desc;  // host copy of the descriptors
+  bool any_force = false;
   int ntiles = 0;
   bool tiles_ready = false;
   double timeout_s = 2.0;
@@ -110,7 +131,31 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 int upload_tiles(lbm_batch* b) {
-  const int bx = kShapes[b->shape][0], by = kShapes[b->shape][1];
+  const BVariant& var = b->vars[b->shape];
+  if (var.kind == 1) {
+    // pipelined kernel: tiles are enumerated from the descriptors
+    long long t = 0;
+    for (int i = 0; i < b->bp.n; ++i) {
+      const Plan& p = b->bp.pl[i];
+      BatchDesc& d = b->desc[i];
+      d.ntx = (p.p.nx + var.X - 1) / var.X;
+      d.tile0 = (int)t;
+      t += (long long)d.ntx * p.p.ny * p.p.nz;
+      if (t >= (1LL << 31)) return ctx_fail(LBM_ERR_UNSUPPORTED, "batch has too many tiles");
+    }
+    b->ntiles = (int)t;
+    int rc = cuda_fail(cudaMemcpyAsync(b->scratch + b->bp.desc_off, b->desc.data(),
+                                       b->desc.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                                       b->stream),
+                       "upload descriptors");
+    if (rc) return rc;
+    rc = cuda_fail(cudaStreamSynchronize(b->stream), "synchronise");
+    if (rc) return rc;
+    b->tiles_ready = true;
+    b->drop_graphs();
+    return LBM_OK;
+  }
+  const int bx = var.bx, by = var.by;
   std::vector<BatchTile> tiles;
   tiles.reserve(b->bp.max_tiles);
   for (int i = 0; i < b->bp.n; ++i) {
@@ -146,9 +191,17 @@ BatchLaunch launch_of(lbm_batch* b, int n) {
   L.bar = b->scratch + kBatchBarrier;
   L.timeout_ns = (long long)(b->timeout_s * 1e9);
   L.collision = b->bp.pl[0].kernel_collision;
-  L.bx = kShapes[b->shape][0];
-  L.by = kShapes[b->shape][1];
-  const int per_sm = b->ops->batch_blocks_per_sm(L.collision, L.bx * L.by);
+  const BVariant& var = b->vars[b->shape];
+  L.kind = var.kind;
+  L.X = var.X;
+  L.stages = var.stages;
+  L.nlat = b->bp.n;
+  L.force = b->any_force;
+  L.bx = var.kind == 0 ? var.bx : 0;
+  L.by = var.kind == 0 ? var.by : 0;
+  const int per_sm = var.kind == 0
+                         ? b->ops->batch_blocks_per_sm(L.collision, L.bx * L.by)
+                         : b->ops->batch_tma_blocks_per_sm(L.collision, L.force, L.X, L.stages);
   int blocks = per_sm * b->sms;
   if (blocks > b->ntiles) blocks = b->ntiles;
   if (blocks < 1) blocks = 1;
@@ -176,7 +229,14 @@ int run_persistent(lbm_batch* b, int n) {
     int rc = cuda_fail(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (rc) return rc;
     cudaError_t e1 = cudaMemsetAsync(b->scratch + kBatchBarrier, 0, sizeof(int) * 4, b->cap);
-    cudaError_t e2 = e1 == cudaSuccess ? b->ops->batch(L) : e1;
+    if (L.blocks < 1 || (L.kind == 1 ? b->ops->batch_tma_blocks_per_sm(L.collision, L.force, L.X,
+                                                                          L.stages)
+                                        : b->ops->batch_blocks_per_sm(L.collision, L.bx * L.by)) < 1) {
+      cudaStreamEndCapture(b->cap, &g);
+      if (g) cudaGraphDestroy(g);
+      return ctx_fail(LBM_ERR_UNSUPPORTED, "batch variant does not fit on a multiprocessor");
+    }
+    cudaError_t e2 = e1 == cudaSuccess ? (L.kind == 1 ? b->ops->batch_tma(L) : b->ops->batch(L)) : e1;
     cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
     if (e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -273,6 +333,10 @@ int lbm_batch_create(int n, const lbm_params* p, void* cuda_stream, lbm_batch** 
     b->views.push_back(v);
   }
   b->ops = ctx_ops(b->views[0]);
+  b->vars = batch_variants(b->ops);
+  b->shape = 0;  // the first pipelined variant where the storage has one
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) b->any_force |= b->bp.pl[i].p.force[a] != 0.0;
   *out = b;
   return LBM_OK;
 }
@@ -287,7 +351,8 @@ int lbm_batch_bind(lbm_batch* b, void* pop_a, void* pop_b, void* scratch) {
   b->scratch = static_cast<char*>(scratch);
   b->cur = 0;
   b->t = 0;
-  std::vector<BatchDesc> desc(b->bp.n);
+  std::vector<BatchDesc>& desc = b->desc;
+  desc.assign(b->bp.n, BatchDesc{});
   for (int i = 0; i < b->bp.n; ++i) {
     const Plan& p = b->bp.pl[i];
     desc[i].g = p.g;
@@ -352,18 +417,20 @@ int lbm_batch_step(lbm_batch* b, int n, int mode) {
 
 int lbm_batch_variant_count(const lbm_batch* b, int* n) {
   if (!b || !n) return ctx_fail(LBM_ERR_ARG, "NULL argument");
-  *n = kNumShapes;
+  *n = (int)b->vars.size();
   return LBM_OK;
 }
 
 int lbm_batch_variant_name(const lbm_batch* b, int v, char* buf, size_t len) {
-  if (!b || !buf || v < 0 || v >= kNumShapes) return ctx_fail(LBM_ERR_ARG, "bad variant");
-  snprintf(buf, len, "tile_b%dx%d", kShapes[v][0], kShapes[v][1]);
+  if (!b || !buf || v < 0 || v >= (int)b->vars.size()) return ctx_fail(LBM_ERR_ARG, "bad variant");
+  const BVariant& var = b->vars[v];
+  if (var.kind == 1) snprintf(buf, len, "tma_X%d_s%d", var.X, var.stages);
+  else snprintf(buf, len, "tile_b%dx%d", var.bx, var.by);
   return LBM_OK;
 }
 
 int lbm_batch_set_variant(lbm_batch* b, int v) {
-  if (!b || v < 0 || v >= kNumShapes) return ctx_fail(LBM_ERR_ARG, "bad variant");
+  if (!b || v < 0 || v >= (int)b->vars.size()) return ctx_fail(LBM_ERR_ARG, "bad variant");
   if (b->shape == v && b->tiles_ready) return LBM_OK;
   b->shape = v;
   if (!b->bound) return LBM_OK;
@@ -385,7 +452,7 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* chosen, float* times_ms) {
   }
   int best = b->shape;
   float best_ms = 1e30f;
-  for (int v = 0; v < kNumShapes && rc == LBM_OK; ++v) {
+  for (int v = 0; v < (int)b->vars.size() && rc == LBM_OK; ++v) {
     rc = lbm_batch_set_variant(b, v);
     if (rc) break;
     rc = run_persistent(b, steps);  // capture + warm-up

@@ -439,6 +439,25 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
 }
 
 static int run_diag(lbm_ctx* c, const double* uref, double* out8) {
+  if (!uref) {
+    // mass, momentum, kinetic energy, enstrophy, flag: two passes over the state
+    double* partials = reinterpret_cast<double*>(c->scratch + kPartialOffset);
+    double* out = reinterpret_cast<double*>(c->scratch + kResultOffset);
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    long long blocks = (long long)c->pl.p.ny * c->pl.p.nz;
+    const long long cap = dev_sms > 0 ? 8LL * dev_sms : 1024;
+    if (blocks > cap) blocks = cap;
+    if (blocks > kMaxPartials) blocks = kMaxPartials;
+    cudaError_t e = c->ops->diag(aux_of(c), c->scratch + c->pl.field_off, partials, (int)blocks, out);
+    c->launches += 3;
+    int rc = cuda_check(e, "diagnostics");
+    if (rc) return rc;
+    rc = cuda_check(cudaMemcpyAsync(out8, out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                    "copy diagnostics");
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  }
   double* fr = reinterpret_cast<double*>(c->scratch + c->pl.field_off);
   double* fu = fr + c->pl.N;
   int rc = lbm_macros(c, fr, fu);
@@ -459,7 +478,7 @@ static int run_diag(lbm_ctx* c, const double* uref, double* out8) {
   if (cap > kMaxPartials) cap = kMaxPartials;
   d.blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
   d.stream = c->stream;
-  cudaError_t e = uref ? diag_l2(d) : diag_sums(d);
+  cudaError_t e = diag_l2(d);
   c->launches += 2;
   rc = cuda_check(e, "diagnostics");
   if (rc) return rc;

@@ -1,5 +1,7 @@
-// diag.cu -- FP64 diagnostics reductions over macroscopic fields and the
-// streaming copy kernel used as the measured bandwidth ceiling.
+// diag.cu -- the FP64 velocity-error reduction over macroscopic fields, the
+// fixed-order reduction of block partials (shared with the diagnostics passes
+// of each lattice/storage unit) and the streaming copy kernel used as the
+// measured bandwidth ceiling.
 //
 // The reductions are deterministic: a fixed grid of blocks accumulates nodes in
 // grid-stride order, reduces warp by warp with shuffles (fixed tree) and writes
@@ -35,60 +37,6 @@ __device__ __forceinline__ void block_store(double (&acc)[NVAL], double* partial
     for (int w = 0; w < DIAG_THREADS / 32; ++w) s += sh[w][threadIdx.x];
     partials[blockIdx.x * NVAL + threadIdx.x] = s;
   }
-}
-
-__device__ __forceinline__ double uval(const double* u, long long N, int a, int D, long long m) {
-  return a < D ? u[a * N + m] : 0.0;
-}
-
-// Per fluid node: mass, momentum, kinetic energy, enstrophy (central differences;
-// across a periodic axis the neighbour wraps, across a non-periodic edge or on a
-// solid node it counts as u = 0) and a not-finite / non-positive density flag.
-__global__ void __launch_bounds__(DIAG_THREADS)
-    k_diag_sums(GeoH G, int D, const double* rho, const double* u, const uint8_t* mask,
-                double* partials) {
-  const long long N = (long long)G.nx * G.ny * G.nz;
-  double acc[NVAL] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const int ext[3] = {G.nx, G.ny, G.nz};
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    if (mask && mask[n]) continue;
-    const int c[3] = {int(n % G.nx), int((n / G.nx) % G.ny), int(n / ((long long)G.nx * G.ny))};
-    const double r = rho[n];
-    double u2 = 0.0;
-    bool bad = !isfinite(r) || !(r > 0.0);
-    for (int a = 0; a < 3; ++a) {
-      const double ua = uval(u, N, a, D, n);
-      bad |= !isfinite(ua);
-      acc[1 + a] += r * ua;
-      u2 += ua * ua;
-    }
-    acc[0] += r;
-    acc[4] += 0.5 * r * u2;
-    double du[3][3];  // du[a][b] = d u_a / d x_b
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) du[a][b] = 0.0;
-    for (int b = 0; b < D; ++b) {
-      double val[2][3];
-      for (int s = 0; s < 2; ++s) {
-        int q[3] = {c[0], c[1], c[2]};
-        q[b] += s ? 1 : -1;
-        bool zero = false;
-        if (q[b] < 0 || q[b] >= ext[b]) {
-          if (G.per[b]) q[b] = q[b] < 0 ? q[b] + ext[b] : q[b] - ext[b];
-          else zero = true;
-        }
-        const long long m = zero ? 0 : ((long long)q[2] * G.ny + q[1]) * G.nx + q[0];
-        if (!zero && mask && mask[m]) zero = true;
-        for (int a = 0; a < 3; ++a) val[s][a] = zero ? 0.0 : uval(u, N, a, D, m);
-      }
-      for (int a = 0; a < 3; ++a) du[a][b] = 0.5 * (val[1][a] - val[0][a]);
-    }
-    const double wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
-    acc[5] += 0.5 * (wx * wx + wy * wy + wz * wz);
-    if (bad) acc[6] = 1.0;
-  }
-  block_store(acc, partials);
 }
 
 // Sums of |u - u_ref|^2 and |u_ref|^2 over fluid nodes.
@@ -133,9 +81,8 @@ __global__ void __launch_bounds__(DIAG_THREADS)
   }
 }
 
-cudaError_t diag_sums(const DiagLaunch& d) {
-  k_diag_sums<<<d.blocks, DIAG_THREADS, 0, d.stream>>>(d.g, d.D, d.rho, d.u, d.mask, d.partials);
-  k_reduce_partials<<<1, DIAG_THREADS, 0, d.stream>>>(d.partials, d.blocks, d.out);
+cudaError_t reduce_partials(const double* partials, int blocks, double* out, cudaStream_t st) {
+  k_reduce_partials<<<1, DIAG_THREADS, 0, st>>>(partials, blocks, out);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,8 @@ struct BatchDesc {
   CoefV<double> cd;
   CoefV<float> cf;
   long long off;  // byte offset of the lattice in each population arena
+  int ntx;        // pipelined kernel: tiles per row at the variant's tile width
+  int tile0;      // pipelined kernel: index of the lattice's first tile
 };
 struct BatchTile {
   int lat, x0, y0, z;
@@ -79,6 +81,9 @@ struct BatchLaunch {
   long long timeout_ns;
   int collision;
   int bx, by, blocks;
+  // pipelined variant (kind 1): tile width, ring depth, lattices, any force
+  int kind, X, stages, nlat;
+  bool force;
   cudaStream_t stream;
 };
 
@@ -92,9 +97,17 @@ struct Ops {
   cudaError_t (*set_pop)(const AuxLaunch&, const double* f);
   cudaError_t (*get_pop)(const AuxLaunch&, double* f);
   cudaError_t (*macros)(const AuxLaunch&, double* rho, double* u);
+  // FP64 diagnostics of the current state: drho and u staged in `fields` in the
+  // arithmetic precision ((1 + D) * N values), block partials [blocks][8]
+  // (blocks <= rows), the eight sums in out[8] (mass, momentum, kinetic energy,
+  // enstrophy, flag, 0)
+  cudaError_t (*diag)(const AuxLaunch&, void* fields, double* partials, int blocks, double* out);
   // persistent batched kernel (cooperative launch) and its occupancy
   cudaError_t (*batch)(const BatchLaunch&);
   int (*batch_blocks_per_sm)(int collision, int threads);
+  // pipelined persistent batched kernel (FP32 arithmetic storages only; else null)
+  cudaError_t (*batch_tma)(const BatchLaunch&);
+  int (*batch_tma_blocks_per_sm)(int collision, bool force, int X, int stages);
   // shared-memory bytes of the pipelined kernel for a tile width and ring depth (0: unsupported)
   size_t (*tma_smem)(int X, int stages);
 };
@@ -161,7 +174,8 @@ struct DiagLaunch {
   int blocks;
   cudaStream_t stream;
 };
-cudaError_t diag_sums(const DiagLaunch&);
+// out[k] = sum over blocks of partials[b][k] in block order (slot 6: maximum).
+cudaError_t reduce_partials(const double* partials, int blocks, double* out, cudaStream_t st);
 cudaError_t diag_l2(const DiagLaunch&);
 cudaError_t copy_ceiling(const void* src, void* dst, size_t bytes, cudaStream_t st);
 

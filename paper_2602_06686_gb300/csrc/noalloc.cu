@@ -11,8 +11,8 @@
 // created with the library and held by every GPU that loads it until the
 // process exits.
 //
-// The array holds at most kNoAllocMaxNodes nodes of FP64 fields (plus the
-// partials and the result); larger lattices are rejected.  Nothing in it is
+// The array holds the staged fields of at most kNoAllocMaxNodes nodes (plus the
+// block partials); larger lattices are rejected.  Nothing in it is
 // read before the same call has written it, so it needs no clearing between
 // calls; it keeps the contents of the last call.  All calls on a device share
 // it, so calls whose work overlaps on the GPU (on different streams) race.
@@ -96,8 +96,7 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_stat
   rc = scratch_address(&base);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  double* rho = base;
-  double* u = base + kNoAllocMaxNodes;
+  void* fields = base;  // drho [N] and u [D][N] in the arithmetic precision
   double* partials = base + 4 * kNoAllocMaxNodes;
 
   AuxLaunch a{};
@@ -110,22 +109,9 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_stat
   a.parity = (int)(steps_done & 1);
   a.stream = st;
   const Ops* ops = ops_for(pl.p.lattice, pl.p.storage);
-  cudaError_t e = ops->macros(a, rho, u);
-  if (e != cudaSuccess) return ctx_fail(LBM_ERR_CUDA, "macros launch failed");
-
-  DiagLaunch d{};
-  d.g = pl.g;
-  d.D = pl.D;
-  d.rho = rho;
-  d.u = u;
-  d.uref = nullptr;
-  d.mask = solid_mask;
-  d.partials = partials;
-  d.out = out;
-  long long want = (pl.N + 255) / 256;
-  d.blocks = (int)(want < 1 ? 1 : (want > kNoAllocBlocks ? kNoAllocBlocks : want));
-  d.stream = st;
-  e = diag_sums(d);
+  long long blocks = (long long)pl.p.ny * pl.p.nz;
+  if (blocks > kNoAllocBlocks) blocks = kNoAllocBlocks;
+  cudaError_t e = ops->diag(a, fields, partials, (int)blocks, out);
   if (e != cudaSuccess) return ctx_fail(LBM_ERR_CUDA, "diagnostics launch failed");
   k_noalloc_finish<<<1, 32, 0, st>>>(out, steps_done);
   e = cudaGetLastError();

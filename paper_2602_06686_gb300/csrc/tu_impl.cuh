@@ -6,6 +6,7 @@
 #include "aa.cuh"
 #include "batch.cuh"
 #include "tma.cuh"
+#include "batch_tma.cuh"
 
 namespace lbm {
 
@@ -53,71 +54,260 @@ __device__ __forceinline__ long long state_slot(const Geo& G, const uint8_t* mas
   return ab_slot<L>(G, mask, x, y, z, i);
 }
 
+// The per-node helper kernels run on a grid of (lattice row, x block): row
+// r = z * ny + y is blockIdx.x, x = blockIdx.y * blockDim.x + threadIdx.x, so
+// no thread divides a 64-bit node index.
+struct RowNode {
+  int x, y, z;
+  long long n;
+  bool valid;
+  __device__ __forceinline__ RowNode(const Geo& G) {
+    const int r = blockIdx.x;
+    x = blockIdx.y * blockDim.x + threadIdx.x;
+    y = r % G.ny;
+    z = r / G.ny;
+    n = (long long)r * G.nx + x;
+    valid = x < G.nx;
+  }
+};
+
 template <class L, class S>
-__global__ void k_init_eq(Geo G, const uint8_t* mask, int layout, int parity,
-                          typename S::T* pop, const double* rho, const double* u, double rho0) {
+__global__ void __launch_bounds__(256) k_init_eq(Geo G, const uint8_t* mask, int layout, int parity,
+                                                 typename S::T* pop, const double* rho,
+                                                 const double* u, double rho0) {
   using R = typename S::R;
   const long long N = (long long)G.nx * G.ny * G.nz;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    if (mask && mask[n]) continue;
-    const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / ((long long)G.nx * G.ny);
-    R f[L::Q];
-    const R ux = R(u[n]), uy = R(u[N + n]), uz = L::D == 3 ? R(u[2 * N + n]) : R(0);
-    feq_shifted<L, R>(R(rho[n] - rho0), ux, uy, uz, f, R(rho0));
+  const RowNode q(G);
+  if (!q.valid || (mask && mask[q.n])) return;
+  const long long n = q.n;
+  R f[L::Q];
+  const R ux = R(u[n]), uy = R(u[N + n]), uz = L::D == 3 ? R(u[2 * N + n]) : R(0);
+  feq_shifted<L, R>(R(rho[n] - rho0), ux, uy, uz, f, R(rho0));
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)] = S::enc(f[i]);
-  }
+  for (int i = 0; i < L::Q; ++i)
+    pop[state_slot<L>(G, mask, layout, parity, q.x, q.y, q.z, i)] = S::enc(f[i]);
 }
 
 template <class L, class S>
-__global__ void k_set_pop(Geo G, const uint8_t* mask, int layout, int parity,
-                          typename S::T* pop, const double* f, double rho0) {
+__global__ void __launch_bounds__(256) k_set_pop(Geo G, const uint8_t* mask, int layout, int parity,
+                                                 typename S::T* pop, const double* f, double rho0) {
   const long long N = (long long)G.nx * G.ny * G.nz;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    if (mask && mask[n]) continue;
-    const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / ((long long)G.nx * G.ny);
+  const RowNode q(G);
+  if (!q.valid || (mask && mask[q.n])) return;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-      pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)] =
-          S::enc(typename S::R(f[i * N + n] - L::w(i) * rho0));
+  for (int i = 0; i < L::Q; ++i)
+    pop[state_slot<L>(G, mask, layout, parity, q.x, q.y, q.z, i)] =
+        S::enc(typename S::R(f[i * N + q.n] - L::w(i) * rho0));
+}
+
+// mode 0: decoded populations f [Q][N]; mode 1: rho [N] and u [D][N] (FP64).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_get(Geo G, const uint8_t* mask, int layout, int parity,
+                                             const typename S::T* pop, double rho0, double Fx,
+                                             double Fy, double Fz, int mode, double* out0,
+                                             double* out1) {
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const RowNode q(G);
+  if (!q.valid) return;
+  const long long n = q.n;
+  const bool solid = mask && mask[n];
+  double g[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i)
+    g[i] = solid ? 0.0 : double(S::dec(pop[state_slot<L>(G, mask, layout, parity, q.x, q.y, q.z, i)]));
+  if (mode == 0) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) out0[i * N + n] = g[i] + L::w(i) * rho0;
+  } else {
+    double drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      drho += g[i];
+      jx += L::cx(i) * g[i];
+      jy += L::cy(i) * g[i];
+      jz += L::cz(i) * g[i];
+    }
+    const double rho = rho0 + drho;
+    out0[n] = rho;
+    out1[n] = solid ? 0.0 : (jx + 0.5 * Fx) / rho;
+    out1[N + n] = solid ? 0.0 : (jy + 0.5 * Fy) / rho;
+    if (L::D == 3) out1[2 * N + n] = solid ? 0.0 : (jz + 0.5 * Fz) / rho;
   }
 }
 
-// mode 0: decoded populations f [Q][N]; mode 1: rho [N] and u [D][N].
-template <class L, class S>
-__global__ void k_get(Geo G, const uint8_t* mask, int layout, int parity, const typename S::T* pop,
-                      double rho0, double Fx, double Fy, double Fz, int mode, double* out0,
-                      double* out1) {
-  const long long N = (long long)G.nx * G.ny * G.nz;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / ((long long)G.nx * G.ny);
-    const bool solid = mask && mask[n];
-    double g[L::Q];
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-      g[i] = solid ? 0.0 : double(S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]));
-    if (mode == 0) {
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) out0[i * N + n] = g[i] + L::w(i) * rho0;
+// ---- diagnostics (two passes and a fixed-order reduction of block partials)
+//
+// Per node, rho and u are formed in the arithmetic precision R of the update
+// (FP32 for FP32/FP16/BF16 storage, FP64 for FP64), from the shifted
+// populations as the collision forms them; every sum over nodes is carried in
+// FP64 across threads and blocks.  Within a thread, FP32 terms are first
+// accumulated with an error-free transformation (TwoSum, Knuth): the running
+// sum s and its rounding error c together carry the exact sum of the terms to
+// within about 2^-48 relative, so nothing is lost before the FP64 stage, and a
+// thread converts to FP64 once instead of once per node (FP64 throughput on
+// GB300 is about 1/60 of FP32).  Blocks own contiguous row ranges, so the
+// result is deterministic.
+template <typename R>
+struct CompSum {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    if constexpr (sizeof(R) == 8) {
+      s += v;
     } else {
-      double drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        drho += g[i];
-        jx += L::cx(i) * g[i];
-        jy += L::cy(i) * g[i];
-        jz += L::cz(i) * g[i];
-      }
-      const double rho = rho0 + drho;
-      out0[n] = rho;
-      out1[n] = solid ? 0.0 : (jx + 0.5 * Fx) / rho;
-      out1[N + n] = solid ? 0.0 : (jy + 0.5 * Fy) / rho;
-      if (L::D == 3) out1[2 * N + n] = solid ? 0.0 : (jz + 0.5 * Fz) / rho;
+      const R t = __fadd_rn(s, v);
+      const R bp = __fsub_rn(t, s);
+      const R e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+      c = __fadd_rn(c, e);
+      s = t;
     }
   }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of K values into partials[blockIdx.x * 8 + k0 + k] (256 threads).
+template <int K>
+__device__ __forceinline__ void block_partials(const double (&acc)[K], double* partials, int k0) {
+  __shared__ double sh[8][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum_d(acc[k]);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
+    partials[blockIdx.x * 8 + k0 + threadIdx.x] = t;
+  }
+}
+
+__device__ __forceinline__ void block_rows(const Geo& G, int& r0, int& r1) {
+  const long long rows = (long long)G.ny * G.nz;
+  r0 = (int)(rows * blockIdx.x / gridDim.x);
+  r1 = (int)(rows * (blockIdx.x + 1) / gridDim.x);
+}
+
+// Pass 1: drho and u into the field scratch (R precision; solid nodes u = 0),
+// and the partial sums of mass, momentum, kinetic energy and the flag.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask, int layout,
+                                                     int parity, const typename S::T* pop,
+                                                     double rho0d, typename S::R Fhx,
+                                                     typename S::R Fhy, typename S::R Fhz,
+                                                     typename S::R* fld, double* partials) {
+  using R = typename S::R;
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const R rho0 = R(rho0d);
+  int r0, r1;
+  block_rows(G, r0, r1);
+  CompSum<R> sm, sx, sy, sz, sk;
+  long long cnt = 0;
+  bool bad = false;
+  int y = r0 % G.ny, z = r0 / G.ny;
+  for (int r = r0; r < r1; ++r) {
+    for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+      const long long n = (long long)r * G.nx + x;
+      if (mask && mask[n]) {
+        fld[n] = R(0);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) fld[(1 + a) * N + n] = R(0);
+        continue;
+      }
+      R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const R g = S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]);
+        drho += g;
+        if (L::cx(i) == 1) jx += g;
+        if (L::cx(i) == -1) jx -= g;
+        if (L::cy(i) == 1) jy += g;
+        if (L::cy(i) == -1) jy -= g;
+        if (L::cz(i) == 1) jz += g;
+        if (L::cz(i) == -1) jz -= g;
+      }
+      const R rho = rho0 + drho;
+      const R ux = (jx + Fhx) / rho, uy = (jy + Fhy) / rho, uz = L::D == 3 ? (jz + Fhz) / rho : R(0);
+      fld[n] = drho;
+      fld[N + n] = ux;
+      fld[2 * N + n] = uy;
+      if (L::D == 3) fld[3 * N + n] = uz;
+      sm.add(drho);
+      sx.add(rho * ux);
+      sy.add(rho * uy);
+      sz.add(rho * uz);
+      sk.add(R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
+      ++cnt;
+      bad |= !isfinite(rho) || !(rho > R(0)) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz);
+    }
+    if (++y == G.ny) {
+      y = 0;
+      ++z;
+    }
+  }
+  const double acc[8] = {double(cnt) * rho0d + sm.value(), sx.value(), sy.value(), sz.value(),
+                         sk.value(), 0.0, bad ? 1.0 : 0.0, 0.0};
+  block_partials<8>(acc, partials, 0);
+}
+
+// Pass 2: enstrophy 1/2 |curl u|^2 with second-order central differences
+// (across a periodic axis the neighbour wraps; across a non-periodic edge or
+// at a solid node it counts as u = 0), into partial slot 5.
+template <typename R, int D>
+__global__ void __launch_bounds__(256) k_diag_enstrophy(Geo G, const uint8_t* mask, const R* fld,
+                                                        double* partials) {
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const R* u = fld + N;
+  int r0, r1;
+  block_rows(G, r0, r1);
+  CompSum<R> se;
+  int y = r0 % G.ny, z = r0 / G.ny;
+  for (int r = r0; r < r1; ++r) {
+    for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+      const long long n = (long long)r * G.nx + x;
+      if (mask && mask[n]) continue;
+      R du[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) du[a][b] = R(0);
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        R val[2][3];
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          int c3[3] = {x, y, z};
+          const int ext = b == 0 ? G.nx : (b == 1 ? G.ny : G.nz);
+          c3[b] += sgn ? 1 : -1;
+          bool zero = false;
+          if (c3[b] < 0 || c3[b] >= ext) {
+            if (G.per[b]) c3[b] = c3[b] < 0 ? c3[b] + ext : c3[b] - ext;
+            else zero = true;
+          }
+          const long long m = zero ? 0 : ((long long)c3[2] * G.ny + c3[1]) * G.nx + c3[0];
+          if (!zero && mask && mask[m]) zero = true;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) val[sgn][a] = (zero || a >= D) ? R(0) : u[a * N + m];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) du[a][b] = R(0.5) * (val[1][a] - val[0][a]);
+      }
+      const R wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
+      se.add(R(0.5) * (wx * wx + wy * wy + wz * wz));
+    }
+    if (++y == G.ny) {
+      y = 0;
+      ++z;
+    }
+  }
+  const double acc[1] = {se.value()};
+  block_partials<1>(acc, partials, 5);
 }
 
 template <class L, class S>
@@ -292,10 +482,20 @@ struct TU {
   }
 
   static dim3 aux_grid(const GeoH& g) {
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    long long b = (N + 255) / 256;
-    if (b > 65536) b = 65536;
-    return dim3((unsigned)b);
+    return dim3((unsigned)((long long)g.ny * g.nz), (unsigned)((g.nx + 255) / 256));
+  }
+
+  static cudaError_t diag(const AuxLaunch& a, void* fields, double* partials, int blocks, double* out) {
+    const Geo G = geo(a.g);
+    R* fld = static_cast<R*>(fields);
+    k_diag_fields<L, S><<<blocks, 256, 0, a.stream>>>(G, a.mask, a.layout, a.parity,
+                                                      static_cast<const T*>(a.pop), a.rho0,
+                                                      R(0.5 * a.F[0]), R(0.5 * a.F[1]),
+                                                      R(0.5 * a.F[2]), fld, partials);
+    k_diag_enstrophy<R, L::D><<<blocks, 256, 0, a.stream>>>(G, a.mask, fld, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return reduce_partials(partials, blocks, out, a.stream);
   }
 
   static cudaError_t init_eq(const AuxLaunch& a, const double* rho, const double* u) {
@@ -363,6 +563,87 @@ struct TU {
     return cudaLaunchKernelExC(&cfg, fn, args);
   }
 
+  // ---- pipelined persistent batched kernel (FP32 arithmetic storages)
+  static size_t batch_tma_smem(int X, int stages) {
+    const int H = 16 / (int)sizeof(T);
+    if ((X != 128 && X != 256) || stages < 2) return 0;
+    const size_t head = 128 * ((2 * (size_t)stages * 8 + 4 + 127) / 128);
+    return head + (size_t)stages * L::Q * (size_t)(X + 2 * H) * sizeof(T);
+  }
+  // Dynamic shared-memory limit set on the batched kernel: enough for the
+  // deepest ring of the variant list (4 stages), and below the opt-in maximum
+  // net of the kernel's static shared memory (grid barrier), so that graphs
+  // captured with any listed depth stay launchable.
+  static int batch_tma_smem_cap(int X) { return (int)batch_tma_smem(X, 4); }
+  template <int COLL, bool FORCE>
+  static void* batch_tma_kernel_cf(int X) {
+    if constexpr (kPack) {
+      if (X == 128) return (void*)&k_batch_tma<L, COLL, S, FORCE, 128>;
+      if (X == 256) return (void*)&k_batch_tma<L, COLL, S, FORCE, 256>;
+    }
+    return nullptr;
+  }
+  template <int COLL>
+  static void* batch_tma_kernel_c(bool force, int X) {
+    return force ? batch_tma_kernel_cf<COLL, true>(X) : batch_tma_kernel_cf<COLL, false>(X);
+  }
+  static void* batch_tma_kernel(int coll, bool force, int X) {
+    switch (coll) {
+      case C_TRT:
+        return batch_tma_kernel_c<C_TRT>(force, X);
+      case C_TRT_RLB:
+        return batch_tma_kernel_c<C_TRT_RLB>(force, X);
+      case C_P_TRT:
+        return batch_tma_kernel_c<C_P_TRT>(force, X);
+    }
+    return nullptr;
+  }
+  static int batch_tma_blocks_per_sm(int coll, bool force, int X, int stages) {
+    void* fn = batch_tma_kernel(coll, force, X);
+    const size_t smem = batch_tma_smem(X, stages);
+    if (!fn || smem == 0 || smem > 227 * 1024) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_tma_smem_cap(X)) !=
+        cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 + X / 2, smem) != cudaSuccess) return 0;
+    return n;
+  }
+  static cudaError_t batch_tma(const BatchLaunch& b) {
+    void* fn = batch_tma_kernel(b.collision, b.force, b.X);
+    const size_t smem = batch_tma_smem(b.X, b.stages);
+    if (!fn || smem == 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_tma_smem_cap(b.X));
+    if (e != cudaSuccess) return e;
+    BatchTmaArgs a;
+    a.desc = b.desc;
+    a.nlat = b.nlat;
+    a.ntiles = b.ntiles;
+    a.A = b.A;
+    a.B = b.B;
+    a.nsteps = b.nsteps;
+    a.parity0 = b.parity0;
+    a.step0 = b.step0;
+    a.flags = b.flags;
+    a.bar = static_cast<BarrierWords*>(b.bar);
+    a.expected = b.expected;
+    a.timeout_ns = b.timeout_ns;
+    a.stages = b.stages;
+    void* args[] = {(void*)&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.blocks);
+    cfg.blockDim = dim3(32 + b.X / 2);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
+
   static const Ops* ops() {
     static Ops o = [] {
       Ops r{};
@@ -378,8 +659,13 @@ struct TU {
       r.set_pop = &set_pop;
       r.get_pop = &get_pop;
       r.macros = &macros;
+      r.diag = &diag;
       r.batch = &batch;
       r.batch_blocks_per_sm = &batch_blocks_per_sm;
+      if (kPack) {
+        r.batch_tma = &batch_tma;
+        r.batch_tma_blocks_per_sm = &batch_tma_blocks_per_sm;
+      }
       r.tma_smem = &tma_smem;
       return r;
     }();
