@@ -535,6 +535,33 @@ def precision_cylinder(steps: int = 0, nx: int = 2048, ny: int = 1024, side: int
     return out
 
 
+def precision_flow(kind: str, n: int, steps: int):
+    """Relative L2 error of the velocity of each storage format against the FP64
+    run of the same workload and length: the decaying 3-D Taylor-Green vortex
+    (D3Q19, Re = 1600, Lambda = 1/4, n^3) or the double shear layer (D2Q9,
+    Re = 1e5, 1/tau- = 1.6, n^2)."""
+    import torch
+    lat = "D3Q19" if kind == "taylor_green_3d" else "D2Q9"
+    rho, u = workload_fields(kind, n)
+    vel = {}
+    for st in PRECISION_STORAGES:
+        g = make_lattice(lat, n, st)
+        g.init_equilibrium(rho, u)
+        g.step(steps)
+        _, uu = g.macros()
+        vel[st] = uu.double().cpu().numpy()
+        rc, _ = g.status()
+        if rc != 0:
+            vel[st] = None
+        del g
+        torch.cuda.empty_cache()
+    out = {"workload": f"{lat} P-TRT {kind} {n}^{3 if lat == 'D3Q19' else 2}, {steps} steps"}
+    for st in ("F32", "F16", "BF16"):
+        out[st] = ({"l2_vs_fp64": rel_l2(vel[st], vel["F64"])} if vel[st] is not None
+                   and vel["F64"] is not None else {"diverged": True})
+    return out
+
+
 def run_precision_study(args):
     """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
     oracle on one column at nu = 0.1), the full-channel throughput per format,
@@ -547,6 +574,8 @@ def run_precision_study(args):
            "channel": precision_channel((0.1, 0.01, 0.001), with_oracle=False),
            "channel_oracle": precision_channel((0.1,), with_oracle=True),
            "throughput": precision_throughput(peak),
+           "taylor_green_3d": precision_flow("taylor_green_3d", 128, 2000),
+           "double_shear": precision_flow("double_shear", 1024, 10240),
            "cylinder": precision_cylinder(args.cyl_steps)}
     torch.cuda.synchronize()
     print(json.dumps(res), flush=True)
@@ -701,6 +730,7 @@ def run_ours(args):
              lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, layout="AA")),
             ("batch256", lambda: batched(peak)),
             ("precision", lambda: {"channel": precision_channel((0.1,)),
+                                   "taylor_green_3d": precision_flow("taylor_green_3d", 96, 1000),
                                    "throughput": precision_throughput(peak)}),
         ]
         for key, fn in jobs:

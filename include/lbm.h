@@ -168,7 +168,11 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f);
  *   1/2 sum rho |u|^2, out[5] enstrophy 1/2 sum |curl u|^2 with second-order
  *   central differences (a neighbour across a periodic axis wraps; across a
  *   non-periodic edge or on a solid node it counts as u = 0), out[6] 1 if any
- *   rho or u is not finite or rho <= 0, out[7] the step counter. */
+ *   rho or u is not finite or rho <= 0, out[7] the step counter.
+ * Per node, rho and u are formed in the update's arithmetic precision (FP32
+ * for FP32/FP16/BF16 storage, FP64 for FP64 storage); the sums over nodes are
+ * exact-rounded per thread (TwoSum) and carried in FP64 across threads and
+ * blocks in a fixed order, so repeated calls on a state are bit-identical. */
 int lbm_diagnostics(lbm_ctx* ctx, double out[8]);
 
 /* Relative L2 error (Sec. 3) of the current velocity against u_ref (device
@@ -283,8 +287,10 @@ int lbm_batch_lattice(lbm_batch* b, int i, lbm_ctx** view);
  * grid barrier gave up (the state is then undefined), after synchronising. */
 int lbm_batch_step(lbm_batch* b, int n, int mode);
 
-/* Tile shape of the persistent kernel (rows x nodes-per-row of one tile),
- * variants and the autotuner, as for single lattices (mode-0 timing). */
+/* Variants of the persistent kernel and the autotuner, as for single lattices
+ * (mode-0 timing).  "tma_X<w>_s<d>" (FP32/FP16/BF16 storage; the default): the
+ * bulk-copy pipeline over row segments of w nodes with a d-stage shared-memory
+ * ring; "tile_b<x>x<y>": register tiles of x nodes by y rows. */
 int lbm_batch_variant_count(const lbm_batch* b, int* n);
 int lbm_batch_variant_name(const lbm_batch* b, int v, char* buf, size_t len);
 int lbm_batch_set_variant(lbm_batch* b, int v);
