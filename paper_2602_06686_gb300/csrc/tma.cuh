@@ -221,8 +221,17 @@ __device__ __forceinline__ void tma_source_row(const Geo& G, int i, int y, int z
   }
 }
 
+// Resident blocks per SM the register allocation is asked to allow: 4 for
+// 16-bit storage (the collision is then the limiter and more warps hide it), 2
+// for FP32, none for FP64 (whose collision needs the registers).  Measured on
+// GB300: +6% (D3Q19 FP16) and +11% (D2Q9 FP32) over no hint.
+template <class S>
+constexpr int tma_min_blocks() {
+  return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
+}
+
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT>
-__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads)
+__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
