@@ -562,6 +562,84 @@ def precision_flow(kind: str, n: int, steps: int):
     return out
 
 
+STABILITY_COLLISIONS = ("P_TRT", "TRT_RLB", "TRT", "RLB", "BGK")
+
+
+def critical_mach(collision: str, cases, n: int = 128, dma: float = 0.01, ma_hi: float = 1.0,
+                  storage: str = "F32"):
+    """Largest stable Mach number Ma_c (Sec. 3.1) of the double shear layer on an
+    n x n periodic lattice for each (Re, 1/tau-) case, by bisection to dma: a run
+    at Ma (u_c = Ma cs, nu = u_c n / Re) is stable if it reaches t = 2 t_c =
+    2 n / u_c steps without divergence (NaN/Inf, rho <= 0 or |u| > 1, the
+    per-lattice flag).  Every bisection round advances all cases together as one
+    batch in one persistent launch.  1/tau- is ignored by BGK and RLB (their
+    minus rate is tied to the plus rate or to 1).  Returns Ma_c per case (0.0:
+    unstable at every tested Ma; ma_hi: stable at ma_hi) and the round count."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Batch
+    cs = 1.0 / math.sqrt(3.0)
+    lo = [0.0] * len(cases)
+    hi = [ma_hi] * len(cases)
+    probe = [ma_hi] * len(cases)  # the first round tries ma_hi itself
+    rounds = 0
+    while True:
+        specs, steps = [], []
+        for (re, itm), ma in zip(cases, probe):
+            uc = ma * cs
+            specs.append(dict(lattice="D2Q9", nx=n, ny=n, nu=uc * n / re, tau_minus=1.0 / itm,
+                              collision=collision, storage=storage))
+            steps.append(int(math.ceil(2.0 * n / uc)))
+        b = Batch(specs)
+        for i in range(len(specs)):
+            b.lattice(i).init_equilibrium(*W.double_shear_rect(n, n, U0=probe[i] * cs))
+        b.step(max(steps), mode=0)
+        torch.cuda.synchronize()
+        for i in range(len(cases)):
+            rc, first = b.lattice(i).status()
+            if rc == 0 or first >= steps[i]:
+                lo[i] = probe[i]
+            else:
+                hi[i] = probe[i]
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        rounds += 1
+        if all(h - l <= dma + 1e-12 or l >= ma_hi for l, h in zip(lo, hi)):
+            break
+        probe = [(l + h) / 2 if h - l > dma + 1e-12 and l < ma_hi else l for l, h in zip(lo, hi)]
+    return lo, rounds
+
+
+def stability_sweep(res=(1e4, 5e4, 1e5, 1e6, 1e7), itms=None, n: int = 128):
+    """Ma_c against 1/tau- for P-TRT, TRT-RLB and TRT (and the single-rate BGK
+    and RLB, whose Ma_c does not depend on tau-) at each Reynolds number."""
+    if itms is None:
+        itms = [round(0.1 * k, 1) for k in range(1, 21)]
+    out = {"n": n, "re": list(res), "inv_tau_minus": itms, "ma_c": {}, "seconds": {},
+           "rounds": {}}
+    for coll in STABILITY_COLLISIONS:
+        grid = [(re, itm) for re in res
+                for itm in (itms if coll in ("P_TRT", "TRT_RLB", "TRT") else [1.0])]
+        t0 = time.perf_counter()
+        mac, rounds = critical_mach(coll, grid, n=n)
+        table = {}
+        for (re, itm), m in zip(grid, mac):
+            table.setdefault(f"{re:g}", {})[f"{itm:g}"] = m
+        out["ma_c"][coll] = table
+        out["seconds"][coll] = time.perf_counter() - t0
+        out["rounds"][coll] = rounds
+    return out
+
+
+def run_stability_study(args):
+    """Critical Mach number sweep of the double shear layer (Sec. 3.1)."""
+    from paper_2602_06686_gb300 import build
+    build.build()
+    print(json.dumps({"study": "stability", **stability_sweep()}), flush=True)
+    return 0
+
+
 def run_precision_study(args):
     """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
     oracle on one column at nu = 0.1), the full-channel throughput per format,
@@ -787,8 +865,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", choices=["precision"], default=None,
-                    help="run the full precision study instead of the benchmark")
+    ap.add_argument("--study", choices=["precision", "stability"], default=None,
+                    help="run the precision study or the critical-Mach stability sweep "
+                         "instead of the benchmark")
     ap.add_argument("--cyl-steps", type=int, default=0,
                     help="square-cylinder steps (0: 30 diffusive e-folds)")
     ap.add_argument("--case", default=None,
@@ -800,6 +879,8 @@ def main():
         return run_case(args)
     if args.study == "precision":
         return run_precision_study(args)
+    if args.study == "stability":
+        return run_stability_study(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
