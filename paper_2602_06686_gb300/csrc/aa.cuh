@@ -16,6 +16,17 @@
 
 namespace lbm {
 
+// One element through the L2-only path (the line may have been written by
+// another SM earlier in the same launch).
+template <typename T>
+__device__ __forceinline__ T ldcg_elem(const T* p) {
+  using Raw = typename RawT<sizeof(T)>::type;
+  const Raw r = __ldcg(reinterpret_cast<const Raw*>(p));
+  T t;
+  memcpy(&t, &r, sizeof(T));
+  return t;
+}
+
 __device__ __forceinline__ int aa_wrap(int s, int n, int per, bool& wall) {
   if (s < 0 || s >= n) {
     if (per) return s < 0 ? s + n : s - n;

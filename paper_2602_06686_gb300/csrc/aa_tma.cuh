@@ -1,0 +1,267 @@
+// aa_tma.cuh -- the in-place AA update (aa.cuh) fed by the bulk-copy pipeline
+// of tma.cuh: one population buffer, read and written by the same launch.
+//
+// Even step (an even number of completed steps): node x reads its own slots
+// (i, x) and writes f*_i(x) to (ibar, x).  The producer copies, per plane i,
+// the tile's own row segment [x0, x0 + X) (no halo); consumers store to the
+// opposite plane of the same row.
+// Odd step: node x reads f_i(x, t) from slot (ibar, x - e_i) -- or (i, x) when
+// x - e_i is beyond a non-periodic edge -- and writes f*_i(x) to (i, x + e_i) --
+// or (ibar, x) when x + e_i is beyond one.  Per plane and tile that is one
+// source row, (y - e_iy, z - e_iz) of plane ibar (or the own row of plane i at a
+// wall), copied with the 16-byte halo exactly like the A/B pull, and one
+// destination row, (y + e_iy, z + e_iz) of plane i shifted by e_ix.
+//
+// In place is race free: the slots node x reads in a step are exactly the slots
+// it writes (its own set, disjoint from every other node's), every one of them
+// has landed in shared memory before the node's consumer stores, and the halo
+// elements a copy brings along that belong to other nodes are never used.
+// Masked lattices use the register kernels of aa.cuh.
+#pragma once
+#include "aa.cuh"
+#include "tma.cuh"
+
+namespace lbm {
+
+template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, bool ODD>
+__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S>())
+    k_step_aa_tma(const TmaArgs<typename S::R> a) {
+  using T = typename S::T;
+  using R = typename S::R;
+  using V = typename std::conditional<PACK, F2, R>::type;
+  using Sh = TmaShape<XT, PACK>;
+  constexpr int HT = 16 / (int)sizeof(T);
+  constexpr int SLOT = XT + 2 * HT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Geo& G = a.g;
+  const int ST = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + ST;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + ST);
+  T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
+  constexpr long long stage_elems = (long long)L::Q * SLOT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_addr(full + s), 1);
+      mbar_init(smem_addr(empty + s), Sh::kConsumerWarps);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* buf = static_cast<T*>(a.dst);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    const unsigned full_mask = 0xffffffffu;
+    TileWalk w(a.ntiles, a.ntx, G.ny);
+    int k = 0;
+    int s = 0;
+    uint32_t u = 0;
+    bool ok = true;
+    for (; w.more(); w.next(), ++k) {
+      if (u > 0 && !mbar_wait_warp(smem_addr(empty + s), (u - 1) & 1u, abort_flag, a.err,
+                                   a.timeout_ns)) {
+        ok = false;
+        break;
+      }
+      const int y = w.y, z = w.z;
+      const int x0 = w.tx * XT;
+      const int xe = min(x0 + XT, G.nx);
+      const int lo = ODD ? max(x0 - HT, 0) : x0;
+      const int hi = ODD ? min(xe + HT, G.nx) : xe;
+      const bool lwrap = ODD && G.per[0] && x0 == 0;
+      const bool rwrap = ODD && G.per[0] && xe == G.nx;
+      const uint32_t main_bytes = (uint32_t)(hi - lo) * sizeof(T);
+      constexpr uint32_t halo_bytes = (uint32_t)HT * sizeof(T);
+      int ys = y, zs = z;
+      bool wall = false;
+      const int i = lane;
+      if (ODD && i < L::Q) tma_source_row_dyn<L>(G, i, y, z, ys, zs, wall);
+      const unsigned walls = __ballot_sync(full_mask, i < L::Q && wall);
+      const uint32_t fb = smem_addr(full + s);
+      if (lane == 0) {
+        const uint32_t nwrap =
+            (uint32_t)(L::Q - __popc(walls)) * ((lwrap ? 1u : 0u) + (rwrap ? 1u : 0u));
+        mbar_arrive_expect_tx(fb, main_bytes * L::Q + nwrap * halo_bytes + (uint32_t)a.extra_tx);
+      }
+      __syncwarp();
+      if (i < L::Q) {
+        T* slot = ring + s * stage_elems + i * SLOT;  // slot[k] holds x = x0 - HT + k
+        // odd: plane ibar of the source row, or at a wall the own slot (i, x);
+        // even: the own slot (i, x)
+        const int pi = (ODD && !wall) ? opp_dyn<L>(i) : i;
+        const long long r = wall ? ((long long)z * G.ny + y) : ((long long)zs * G.ny + ys);
+        const T* rowp = buf + pi * G.plane + r * G.pitch;
+        bulk_g2s(smem_addr(slot + (lo - (x0 - HT))), rowp + lo, main_bytes, fb);
+        if (ODD && !wall) {
+          if (lwrap) bulk_g2s(smem_addr(slot), rowp + G.nx - HT, halo_bytes, fb);
+          if (rwrap) bulk_g2s(smem_addr(slot + HT + (G.nx - x0)), rowp, halo_bytes, fb);
+        }
+      }
+      if (++s == ST) {
+        s = 0;
+        ++u;
+      }
+    }
+    if (!ok && lane == 0) {
+      // let every issued copy land before the block's shared memory is released
+      for (int kk = (k > ST ? k - ST : 0); kk < k; ++kk)
+        mbar_wait(smem_addr(full + kk % ST), (uint32_t)((kk / ST) & 1), abort_flag, a.err,
+                  a.timeout_ns, false);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  constexpr int NPT = Sh::kNPT;
+  constexpr bool ADJ = PACK && sizeof(T) == 2;
+  const int ct = threadIdx.x - 32;
+  int jn[NPT];
+  jn[0] = ADJ ? 2 * ct : ct;
+  if (PACK) jn[NPT - 1] = ADJ ? 2 * ct + 1 : ct + XT / 2;
+  TileWalk w(a.ntiles, a.ntx, G.ny);
+  int s = 0;
+  uint32_t u = 0;
+  for (; w.more(); w.next()) {
+    if (!mbar_wait_warp(smem_addr(full + s), u & 1u, abort_flag, a.err, a.timeout_ns)) break;
+    const int y = w.y, z = w.z;
+    const int x0 = w.tx * XT;
+    const int wdt = min(XT, G.nx - x0);
+    const T* st = ring + s * stage_elems;
+    const long long own = ((long long)z * G.ny + y) * G.pitch;
+    // odd step: does the tile touch a wall row / plane, or an x wall?
+    const bool anywall = ODD && ((!G.per[1] && (y == 0 || y == G.ny - 1)) ||
+                                 (L::D == 3 && !G.per[2] && (z == 0 || z == G.nz - 1)));
+    const bool xwall = ODD && !G.per[0] && (x0 == 0 || x0 + XT >= G.nx);
+    bool act[NPT];
+#pragma unroll
+    for (int n = 0; n < NPT; ++n) act[n] = jn[n] < wdt;
+    V g[L::Q];
+    if (!anywall && !xwall) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int sh = ODD ? L::cx(i) : 0;
+        const T* slot = st + i * SLOT + HT - sh;
+        if constexpr (ADJ) {
+          if (sh == 0) {
+            float a0, a1;
+            S::dec2(*reinterpret_cast<const uint32_t*>(slot + jn[0]), a0, a1);
+            g[i] = F2{a0, a1};
+          } else {
+            g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[NPT - 1]])};
+          }
+        } else if constexpr (PACK) {
+          g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[NPT - 1]])};
+        } else {
+          g[i] = S::dec(slot[jn[0]]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int ex = L::cx(i);
+        const T* slot = st + i * SLOT + HT;
+        int ys, zs;
+        bool wallrow;
+        tma_source_row<L>(G, i, y, z, ys, zs, wallrow);
+        R v[NPT];
+#pragma unroll
+        for (int n = 0; n < NPT; ++n) {
+          const int j = jn[n];
+          const int x = x0 + j;
+          if (wallrow) {
+            v[n] = S::dec(slot[j]);  // the own slot (i, x) was copied
+          } else if (!G.per[0] && ((ex == 1 && x == 0) || (ex == -1 && x == G.nx - 1))) {
+            // x - e_i beyond an x wall: the own slot (i, x), which only this node touches
+            v[n] = act[n] ? S::dec(ldcg_elem(buf + i * G.plane + own + x)) : R(0);
+          } else {
+            v[n] = S::dec(slot[j - ex]);
+          }
+        }
+        if constexpr (PACK) {
+          g[i] = F2{v[0], v[NPT - 1]};
+        } else {
+          g[i] = v[0];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(empty + s));
+    if (++s == ST) {
+      s = 0;
+      ++u;
+    }
+    const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
+    bool anybad = act[0] && (bad & 1u);
+    if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
+    R out[NPT];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if constexpr (PACK) {
+        out[0] = g[i].x;
+        out[NPT - 1] = g[i].y;
+      } else {
+        out[0] = g[i];
+      }
+      if constexpr (!ODD) {
+        // even: f*_i(x) into the opposite slot of the node's own row
+        T* op = buf + L::opp(i) * G.plane + own + x0;
+        if constexpr (ADJ) {
+          if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(out[0], out[NPT - 1]);
+          else if (act[0]) op[jn[0]] = S::enc(out[0]);
+        } else {
+#pragma unroll
+          for (int n = 0; n < NPT; ++n)
+            if (act[n]) op[jn[n]] = S::enc(out[n]);
+        }
+      } else {
+        // odd: f*_i(x) into slot (i, x + e_i), or (ibar, x) beyond a wall
+        const int ex = L::cx(i);
+        int yd = y + L::cy(i), zd = z + L::cz(i);
+        bool rwall = false;
+        if (yd < 0 || yd >= G.ny) {
+          if (G.per[1]) yd = yd < 0 ? yd + G.ny : yd - G.ny;
+          else rwall = true;
+        }
+        if (zd < 0 || zd >= G.nz) {
+          if (G.per[2]) zd = zd < 0 ? zd + G.nz : zd - G.nz;
+          else rwall = true;
+        }
+        T* rowd = buf + i * G.plane + ((long long)zd * G.ny + yd) * G.pitch;
+        T* rowo = buf + L::opp(i) * G.plane + own;
+        bool done = false;
+        if constexpr (ADJ) {
+          if (ex == 0 && !rwall) {
+            if (act[NPT - 1])
+              *reinterpret_cast<uint32_t*>(rowd + x0 + jn[0]) = S::enc2(out[0], out[NPT - 1]);
+            else if (act[0])
+              rowd[x0 + jn[0]] = S::enc(out[0]);
+            done = true;
+          }
+        }
+        if (!done) {
+#pragma unroll
+          for (int n = 0; n < NPT; ++n) {
+            if (!act[n]) continue;
+            const int x = x0 + jn[n];
+            int xd = x + ex;
+            bool wl = rwall;
+            if (xd < 0 || xd >= G.nx) {
+              if (G.per[0]) xd = xd < 0 ? xd + G.nx : xd - G.nx;
+              else wl = true;
+            }
+            if (wl) rowo[x] = S::enc(out[n]);
+            else rowd[xd] = S::enc(out[n]);
+          }
+        }
+      }
+    }
+    record_bad(a.flag, a.step, anybad);
+  }
+}
+
+}  // namespace lbm

@@ -19,6 +19,7 @@
 // copies (the async proxy): the grid barrier orders the two at GPU scope and
 // a proxy fence on both sides of it orders them across the proxies.
 #pragma once
+#include "aa.cuh"
 #include "batch.cuh"
 #include "tma.cuh"
 
@@ -87,17 +88,6 @@ struct BatchWalk {
     if (lat + 1 < nlat) load(desc, lat + 1);
   }
 };
-
-// One element through the L2-only path (the line may have been written by
-// another SM earlier in the same launch).
-template <typename T>
-__device__ __forceinline__ T ldcg_elem(const T* p) {
-  using Raw = typename RawT<sizeof(T)>::type;
-  const Raw r = __ldcg(reinterpret_cast<const Raw*>(p));
-  T t;
-  memcpy(&t, &r, sizeof(T));
-  return t;
-}
 
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");

@@ -122,9 +122,9 @@ int plan(const lbm_params* p, Plan* out) {
 std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked) {
   static const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
   std::vector<Variant> v;
-  // pipelined bulk-copy kernel: A/B layout, no solid mask, rows a multiple of 16 bytes
+  // pipelined bulk-copy kernel (A/B or AA): no solid mask, rows a multiple of 16 bytes
   const int H = 16 / pl.esize;
-  if (pl.p.layout == LBM_LAYOUT_AB && !masked && pl.p.nx % H == 0 && pl.p.nx >= 2 * H) {
+  if (!masked && pl.p.nx % H == 0 && pl.p.nx >= 2 * H) {
     static const int tiles[] = {512, 384, 256, 192, 128};
     static const int depths[] = {4, 3, 6, 8, 2};
     for (int X : tiles)

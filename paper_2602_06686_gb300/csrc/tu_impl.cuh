@@ -7,6 +7,7 @@
 #include "batch.cuh"
 #include "tma.cuh"
 #include "batch_tma.cuh"
+#include "aa_tma.cuh"
 
 namespace lbm {
 
@@ -389,18 +390,28 @@ struct TU {
     a.timeout_ns = s.wait_ns > 0 ? s.wait_ns : 2000000000LL;
     a.extra_tx = s.extra_tx;
     const size_t smem = tma_smem(XT, a.stages);
-    if (smem == 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = &k_step_tma<L, COLL, S, FORCE, kPack, XT>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
+    if (smem == 0 || smem > 227 * 1024 || a.stages > 8) return cudaErrorInvalidValue;
+    // 0: A/B, 1: AA even step, 2: AA odd step
+    const int kind = s.layout == 1 ? 1 + (s.parity & 1) : 0;
+    void (*kern)(TmaArgs<R>) = kind == 0   ? &k_step_tma<L, COLL, S, FORCE, kPack, XT>
+                               : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
+                                           : &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>;
+    // per instantiation and kind: the shared-memory opt-in (once) and the
+    // resident blocks per SM for each ring depth (cached)
+    static bool attr_set[3] = {false, false, false};
+    static int per_sm_cache[3][9] = {};
+    if (!attr_set[kind]) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       if (e != cudaSuccess) return e;
-      attr_set = true;
+      attr_set[kind] = true;
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int per_sm = per_sm_cache[kind][a.stages];
+    if (per_sm == 0) {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      per_sm_cache[kind][a.stages] = per_sm;
+    }
     long long blocks = (long long)per_sm * (s.sms > 0 ? s.sms : 1);
     if (blocks > a.ntiles) blocks = a.ntiles;
     kern<<<(unsigned)blocks, Sh::kThreads, smem, s.stream>>>(a);
@@ -437,7 +448,7 @@ struct TU {
   }
 
   static cudaError_t step_tma(const StepLaunch& s) {
-    if (s.mask != nullptr || s.layout != 0) return cudaErrorInvalidValue;
+    if (s.mask != nullptr) return cudaErrorInvalidValue;
     switch (s.collision) {
       case C_TRT:
         return tma_coll<C_TRT>(s);
