@@ -614,8 +614,8 @@ def critical_mach(collision: str, cases, n: int = 128, dma: float = 0.01, ma_hi:
 def stability_sweep(res=(1e4, 5e4, 1e5, 1e6, 1e7), itms=None, n: int = 128):
     """Ma_c against 1/tau- for P-TRT, TRT-RLB and TRT (and the single-rate BGK
     and RLB, whose Ma_c does not depend on tau-) at each Reynolds number."""
-    if itms is None:
-        itms = [round(0.1 * k, 1) for k in range(1, 21)]
+    if itms is None:  # 0.1 .. 1.9 and 1.99 (1/tau- = 2 is tau- = 1/2, not a valid rate)
+        itms = [round(0.1 * k, 1) for k in range(1, 20)] + [1.99]
     out = {"n": n, "re": list(res), "inv_tau_minus": itms, "ma_c": {}, "seconds": {},
            "rounds": {}}
     for coll in STABILITY_COLLISIONS:

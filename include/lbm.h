@@ -244,11 +244,13 @@ int lbm_set_variant(lbm_ctx* ctx, int v);
 
 /* Times every variant (reps steps each, CUDA events, after one warm-up) and
  * selects the fastest; *chosen (may be NULL) receives it, times_ms (may be
- * NULL, length lbm_variant_count) the per-step times.  The state is not
- * changed: trial steps read the current buffer and write the other one, which
- * the next step overwrites.  A/B layout only (AA returns LBM_ERR_UNSUPPORTED).
- * Results are cached per (lattice, storage, collision, mask, extent) for the
- * process.  Synchronises. */
+ * NULL, length lbm_variant_count) the per-step times.  A/B layout: the state
+ * is not changed (trial steps read the current buffer and write the other one,
+ * which the next step overwrites).  AA layout: there is no spare buffer, so the
+ * trials are real steps in pairs (even, odd): the lattice advances by
+ * 2 (reps + 1) steps per variant and the step counter with it.  Results are
+ * cached per (lattice, storage, collision, mask, extent, layout) for the
+ * process; a cached answer (times_ms NULL) runs nothing.  Synchronises. */
 int lbm_autotune(lbm_ctx* ctx, int reps, int* chosen, float* times_ms);
 
 int lbm_destroy(lbm_ctx* ctx);

@@ -597,14 +597,14 @@ int lbm_set_variant(lbm_ctx* c, int v) {
 
 int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   CHECK_CTX(c);
-  if (c->pl.p.layout != LBM_LAYOUT_AB) return fail(LBM_ERR_UNSUPPORTED, "autotune needs the A/B layout");
   if (reps < 1) reps = 1;
-  using Key = std::tuple<int, int, int, int, int, int, int, int, int, int>;
+  const bool aa = c->pl.p.layout == LBM_LAYOUT_AA;
+  using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
   static std::mutex mu;
   static std::map<Key, int> cache;
   const Key key{c->pl.p.lattice, c->pl.p.storage, c->pl.kernel_collision, c->mask != nullptr,
                 c->pl.p.nx,      c->pl.p.ny,      c->pl.p.nz,            c->pl.g.per[0],
-                c->pl.g.per[1],  c->pl.g.per[2]};
+                c->pl.g.per[1],  c->pl.g.per[2],        c->pl.p.layout};
   if (!times_ms) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -624,12 +624,25 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   }
   int best = c->var;
   float best_ms = 1e30f;
+  const int keep = c->var;
   for (int v = 0; v < (int)c->vars.size() && rc == LBM_OK; ++v) {
-    StepLaunch sl = step_of(c, c->vars[v]);  // reads the state, writes the other buffer
-    cudaError_t e = c->ops->step(sl);
-    c->launches += 1 + reps;
-    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = c->ops->step(sl);
+    cudaError_t e = cudaSuccess;
+    if (!aa) {
+      StepLaunch sl = step_of(c, c->vars[v]);  // reads the state, writes the other buffer
+      e = c->ops->step(sl);
+      c->launches += 1 + reps;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = c->ops->step(sl);
+    } else {
+      // in place there is no spare buffer: time pairs of (even, odd) steps that
+      // really advance the lattice
+      c->var = v;
+      rc = ctx_step(c, 2);
+      if (rc) break;
+      e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) rc = ctx_step(c, 2 * reps);
+      if (rc) break;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -638,7 +651,7 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
       rc = fail(LBM_ERR_CUDA, "autotune", e);
       break;
     }
-    ms /= reps;
+    ms /= aa ? 2 * reps : reps;
     if (times_ms) times_ms[v] = ms;
     if (ms < best_ms) {
       best_ms = ms;
@@ -647,7 +660,10 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
+  if (rc) {
+    c->var = keep;
+    return rc;
+  }
   c->var = best;
   {
     std::lock_guard<std::mutex> lk(mu);

@@ -214,6 +214,27 @@ def test_autotune_keeps_state_and_picks_a_variant():
     assert np.array_equal(g.populations().cpu().numpy(), ref.populations().cpu().numpy())
 
 
+def test_autotune_aa_advances_in_steps_and_stays_consistent():
+    """In place the trials are real (even, odd) step pairs: the lattice advances
+    by 2 (reps + 1) steps per variant, and the state equals an A/B run of the
+    same total length."""
+    shape = (1, 32, 128)
+    rng = np.random.default_rng(37)
+    rho, u = W.random_macros(shape, 2, rng)
+    g = gpu_lattice(O.D2Q9, shape, O.TRT, 0.03, 0.25, storage="F32", layout="AA")
+    g.init_equilibrium(rho, u)
+    g.step(1)
+    nvar = len(g.variants())
+    chosen, times = g.autotune(reps=2)
+    assert 0 <= chosen < nvar and g.variant == chosen and all(t > 0 for t in times)
+    assert g.t == 1 + nvar * 2 * 3
+    g.step(1)
+    ref = gpu_lattice(O.D2Q9, shape, O.TRT, 0.03, 0.25, storage="F32")
+    ref.init_equilibrium(rho, u)
+    ref.step(g.t)
+    assert np.array_equal(g.populations().cpu().numpy(), ref.populations().cpu().numpy())
+
+
 def test_copy_kernel_copies():
     import torch
     from paper_2602_06686_gb300 import copy_ceiling
