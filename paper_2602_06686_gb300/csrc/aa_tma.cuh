@@ -198,6 +198,11 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
     const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
     bool anybad = act[0] && (bad & 1u);
     if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
+    // odd step, tile away from every row end and boundary row / plane: the
+    // destination (i, x + e_i) is a fixed offset from the node, no wrap, no wall
+    const bool inner = ODD && x0 > 0 && x0 + XT < G.nx && y > 0 && y < G.ny - 1 &&
+                       (L::D == 2 || (z > 0 && z < G.nz - 1));
+    const long long zstride = (long long)G.ny * G.pitch;
     R out[NPT];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -214,6 +219,21 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
           if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(out[0], out[NPT - 1]);
           else if (act[0]) op[jn[0]] = S::enc(out[0]);
         } else {
+#pragma unroll
+          for (int n = 0; n < NPT; ++n)
+            if (act[n]) op[jn[n]] = S::enc(out[n]);
+        }
+      } else if (inner) {
+        T* op = buf + i * G.plane + own + L::cz(i) * zstride + L::cy(i) * G.pitch + L::cx(i) + x0;
+        bool done = false;
+        if constexpr (ADJ) {
+          if (L::cx(i) == 0) {
+            if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(out[0], out[NPT - 1]);
+            else if (act[0]) op[jn[0]] = S::enc(out[0]);
+            done = true;
+          }
+        }
+        if (!done) {
 #pragma unroll
           for (int n = 0; n < NPT; ++n)
             if (act[n]) op[jn[n]] = S::enc(out[n]);
