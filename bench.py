@@ -262,14 +262,18 @@ def workload_fields(kind: str, n: int):
     return W.taylor_green_3d(n, u0=0.05)
 
 
-def make_lattice(lat: str, n: int, storage: str, collision: str = "P_TRT", layout: str = "AB"):
+def make_lattice(lat: str, n: int, storage: str, collision: str = "P_TRT", layout: str = "AB",
+                 tau_minus: float | None = None):
+    """D2Q9: double shear layer, Re = U0 N / nu = 1e5, 1/tau- = 1.6 (the stability
+    optimum of Sec. 3.1).  D3Q19: Taylor-Green vortex at Re = 1600 (L = N / 2 pi),
+    Lambda = 1/4 unless tau_minus is given."""
     from paper_2602_06686_gb300 import Lattice
     if lat == "D2Q9":
-        # double shear layer: Re = U0 N / nu = 1e5, 1/tau- = 1.6 (the stability optimum of Sec. 3.1)
         return Lattice(lattice="D2Q9", nx=n, ny=n, nz=1, nu=0.1 * n / 1e5, tau_minus=1 / 1.6,
                        collision=collision, storage=storage, layout=layout)
+    rates = dict(tau_minus=tau_minus) if tau_minus else dict(Lambda=0.25)
     return Lattice(lattice="D3Q19", nx=n, ny=n, nz=n, nu=0.05 * n / (2 * math.pi * 1600),
-                   Lambda=0.25, collision=collision, storage=storage, layout=layout)
+                   collision=collision, storage=storage, layout=layout, **rates)
 
 
 def time_kernel(lat_obj, inner: int, reps: int):
@@ -537,15 +541,16 @@ def precision_cylinder(steps: int = 0, nx: int = 2048, ny: int = 1024, side: int
 
 def precision_flow(kind: str, n: int, steps: int):
     """Relative L2 error of the velocity of each storage format against the FP64
-    run of the same workload and length: the decaying 3-D Taylor-Green vortex
-    (D3Q19, Re = 1600, Lambda = 1/4, n^3) or the double shear layer (D2Q9,
-    Re = 1e5, 1/tau- = 1.6, n^2)."""
+    run of the same workload and length: the 3-D Taylor-Green vortex (D3Q19,
+    Re = 1600, n^3, 1/tau- = 1.6: with Lambda = 1/4 the minus rate is tiny at
+    this Reynolds number and the run diverges, see taylor_green_run) or the
+    double shear layer (D2Q9, Re = 1e5, 1/tau- = 1.6, n^2)."""
     import torch
     lat = "D3Q19" if kind == "taylor_green_3d" else "D2Q9"
     rho, u = workload_fields(kind, n)
     vel = {}
     for st in PRECISION_STORAGES:
-        g = make_lattice(lat, n, st)
+        g = make_lattice(lat, n, st, tau_minus=1 / 1.6 if lat == "D3Q19" else None)
         g.init_equilibrium(rho, u)
         g.step(steps)
         _, uu = g.macros()
@@ -640,6 +645,31 @@ def run_stability_study(args):
     return 0
 
 
+def taylor_green_run(n: int = 384, steps: int = 2000, every: int = 100):
+    """The 3-D Taylor-Green vortex at Re = 1600 on n^3 (u0 = 0.05), 2000 steps,
+    kinetic energy and enstrophy reduced in FP64 every `every` steps: FP32
+    storage with Lambda = 1/4 and with 1/tau- = 1.6, and FP64 storage with
+    1/tau- = 1.6.  Reports the histories and the first diverged step."""
+    import torch
+    rho, u = workload_fields("taylor_green_3d", n)
+    out = {"workload": f"D3Q19 P-TRT Taylor-Green {n}^3, Re = 1600, u0 = 0.05, {steps} steps"}
+    for name, st, tm in (("F32_Lambda_1/4", "F32", None), ("F32_inv_tau_minus_1.6", "F32", 1 / 1.6),
+                         ("F64_inv_tau_minus_1.6", "F64", 1 / 1.6)):
+        g = make_lattice("D3Q19", n, st, tau_minus=tm)
+        g.init_equilibrium(rho, u)
+        ke, ens = [], []
+        for _ in range(steps // every):
+            g.step(every)
+            d = g.diagnostics()
+            ke.append(d["kinetic_energy"])
+            ens.append(d["enstrophy"])
+        rc, first = g.status()
+        out[name] = {"kinetic_energy": ke, "enstrophy": ens, "first_diverged_step": first}
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_precision_study(args):
     """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
     oracle on one column at nu = 0.1), the full-channel throughput per format,
@@ -653,6 +683,7 @@ def run_precision_study(args):
            "channel_oracle": precision_channel((0.1,), with_oracle=True),
            "throughput": precision_throughput(peak),
            "taylor_green_3d": precision_flow("taylor_green_3d", 128, 2000),
+           "taylor_green_384": taylor_green_run(),
            "double_shear": precision_flow("double_shear", 1024, 10240),
            "cylinder": precision_cylinder(args.cyl_steps)}
     torch.cuda.synchronize()
