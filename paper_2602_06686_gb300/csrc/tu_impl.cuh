@@ -211,8 +211,25 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
   CompSum<R> sm, sx, sy, sz, sk;
   long long cnt = 0;
   bool bad = false;
+  // A/B layout without a mask: the source row of every plane is fixed for a
+  // row, so it is resolved once per row instead of once per node and plane
+  const bool rowwise = layout == 0 && mask == nullptr;
   int y = r0 % G.ny, z = r0 / G.ny;
   for (int r = r0; r < r1; ++r) {
+    const long long own = ((long long)z * G.ny + y) * G.pitch;
+    const T* rowp[L::Q];
+    unsigned wallrows = 0u;
+    if (rowwise) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        int ys, zs;
+        bool wall;
+        tma_source_row<L>(G, i, y, z, ys, zs, wall);
+        rowp[i] = wall ? pop + L::opp(i) * G.plane + own
+                       : pop + i * G.plane + ((long long)zs * G.ny + ys) * G.pitch;
+        if (wall) wallrows |= 1u << i;
+      }
+    }
     for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
       const long long n = (long long)r * G.nx + x;
       if (mask && mask[n]) {
@@ -224,7 +241,26 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
       R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        const R g = S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]);
+        R g;
+        if (rowwise) {
+          if (wallrows & (1u << i)) {
+            g = S::dec(rowp[i][x]);  // beyond a wall: the node's own opposite slot
+          } else {
+            int xs = x - L::cx(i);
+            if (xs < 0 || xs >= G.nx) {
+              if (G.per[0]) {
+                xs = xs < 0 ? xs + G.nx : xs - G.nx;
+                g = S::dec(rowp[i][xs]);
+              } else {
+                g = S::dec(pop[L::opp(i) * G.plane + own + x]);
+              }
+            } else {
+              g = S::dec(rowp[i][xs]);
+            }
+          }
+        } else {
+          g = S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]);
+        }
         drho += g;
         if (L::cx(i) == 1) jx += g;
         if (L::cx(i) == -1) jx -= g;
@@ -234,7 +270,8 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
         if (L::cz(i) == -1) jz -= g;
       }
       const R rho = rho0 + drho;
-      const R ux = (jx + Fhx) / rho, uy = (jy + Fhy) / rho, uz = L::D == 3 ? (jz + Fhz) / rho : R(0);
+      const R inv = R(1) / rho;
+      const R ux = (jx + Fhx) * inv, uy = (jy + Fhy) * inv, uz = L::D == 3 ? (jz + Fhz) * inv : R(0);
       fld[n] = drho;
       fld[N + n] = ux;
       fld[2 * N + n] = uy;
