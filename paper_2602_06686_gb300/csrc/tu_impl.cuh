@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
   int y = r0 % G.ny, z = r0 / G.ny;
   for (int r = r0; r < r1; ++r) {
     const long long own = ((long long)z * G.ny + y) * G.pitch;
-    const T* rowp[L::Q];
+    const typename S::T* rowp[L::Q];
     unsigned wallrows = 0u;
     if (rowwise) {
 #pragma unroll
