@@ -692,7 +692,7 @@ def run_precision_study(args):
 
 
 def run_case(args):
-    """One lattice configuration for a profiler: LATTICE:STORAGE:NX,NY,NZ[:COLLISION],
+    """One lattice configuration for a profiler: LATTICE:STORAGE:NX,NY,NZ[:COLLISION[:LAYOUT]],
     fixed kernel variant (by name; the default variant otherwise), ``--warmup``
     updates then ``--inner`` updates."""
     import torch
@@ -703,15 +703,16 @@ def run_case(args):
     lat, st = parts[0], parts[1]
     dims = [int(v) for v in parts[2].split(",")]
     coll = parts[3] if len(parts) > 3 else "P_TRT"
+    layout = parts[4] if len(parts) > 4 else "AB"
     nx, ny = dims[0], dims[1]
     nz = dims[2] if len(dims) > 2 else 1
     if lat == "D2Q9":
         g = Lattice(lattice="D2Q9", nx=nx, ny=ny, nu=0.1 * nx / 1e5, tau_minus=1 / 1.6,
-                    collision=coll, storage=st)
+                    collision=coll, storage=st, layout=layout)
         rho, u = W.double_shear_rect(nx, ny)
     else:
         g = Lattice(lattice="D3Q19", nx=nx, ny=ny, nz=nz, nu=0.05 * nx / (2 * math.pi * 1600),
-                    Lambda=0.25, collision=coll, storage=st)
+                    Lambda=0.25, collision=coll, storage=st, layout=layout)
         rho, u = W.channel_at_rest((nz, ny, nx), 3)
         u[0] = 0.02
     g.init_equilibrium(rho, u)
@@ -902,7 +903,7 @@ def main():
     ap.add_argument("--cyl-steps", type=int, default=0,
                     help="square-cylinder steps (0: 30 diffusive e-folds)")
     ap.add_argument("--case", default=None,
-                    help="LATTICE:STORAGE:NX,NY,NZ[:COLLISION]: run one configuration "
+                    help="LATTICE:STORAGE:NX,NY,NZ[:COLLISION[:LAYOUT]]: run one configuration "
                          "(--warmup + --inner updates) for a profiler and exit")
     ap.add_argument("--variant", default=None, help="kernel variant name for --case")
     args = ap.parse_args()
