@@ -192,3 +192,57 @@ def test_pipelined_variants_match_register_variants(lat, shape, storage, periodi
     want = O.step(p, O.init_equilibrium(p, rho, u), 9)
     tol = {"F64": 1e-12, "F32": 2e-6, "F16": 2e-3, "BF16": 2e-2}[storage]
     assert elem_rel(ref, want) < tol
+
+
+@pytest.mark.parametrize("lat,shape,periodic", [
+    (O.D2Q9, (1, 1, 1), (1, 1, 1)),     # one node: every neighbour is itself
+    (O.D2Q9, (1, 1, 5), (1, 0, 1)),     # one row between two walls
+    (O.D2Q9, (1, 6, 1), (0, 1, 1)),     # one column between two walls
+    (O.D3Q19, (1, 1, 1), (1, 1, 1)),
+    (O.D3Q19, (1, 3, 2), (0, 0, 0)),    # closed box one plane thick
+    (O.D3Q19, (2, 1, 7), (1, 0, 1)),
+])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_degenerate_extents_match_oracle(lat, shape, periodic, storage):
+    """Extents of one or two nodes on an axis, periodic (a node is its own
+    neighbour) or walled on both sides, with a force: every variant the library
+    offers for the shape agrees with the oracle (FP64 to 1e-12 in the
+    populations, FP32 to 2e-5 in rho and u)."""
+    rng = np.random.default_rng(28)
+    rho, u = W.random_macros(shape, O.D_OF[lat], rng, umax=0.05)
+    F = (1e-4, -2e-5, 3e-5 if lat == O.D3Q19 else 0.0)
+    g = gpu_lattice(lat, shape, O.P_TRT, 0.05, 3 / 16, storage=storage, force=F, periodic=periodic)
+    p = oracle_params(lat, shape, O.P_TRT, 0.05, 3 / 16, force=F, periodic=periodic)
+    ref = O.step(p, O.init_equilibrium(p, rho, u), 17)
+    r_ref, u_ref = O.macros(p, ref)
+    for v in range(len(g.variants())):
+        g.variant = v
+        g.init_equilibrium(rho, u)
+        g.step(17)
+        assert g.status()[0] == 0
+        if storage == "F64":
+            assert elem_rel(g.populations().cpu().numpy(), ref) < 1e-12, g.variants()[v]
+        else:
+            r_gpu, u_gpu = (t.cpu().numpy() for t in g.macros())
+            assert elem_rel(r_gpu, r_ref) < 2e-5
+            assert scaled_err(u_gpu, u_ref) < 2e-5
+
+
+def test_zero_steps_and_empty_batch_of_steps():
+    """lbm_step(0) and lbm_batch_step(0) are no-ops: the state and the step
+    counter are unchanged."""
+    from paper_2602_06686_gb300 import Batch
+    shape = (1, 8, 16)
+    rng = np.random.default_rng(29)
+    rho, u = W.random_macros(shape, 2, rng, umax=0.05)
+    g = gpu_lattice(O.D2Q9, shape, O.P_TRT, 0.05, 0.25, storage="F32")
+    g.init_equilibrium(rho, u)
+    before = g.populations().cpu().numpy()
+    g.step(0)
+    assert g.t == 0 and np.array_equal(g.populations().cpu().numpy(), before)
+    b = Batch([dict(lattice="D2Q9", nx=16, ny=8, nu=0.05, Lambda=0.25, collision="P_TRT",
+                    storage="F32")])
+    b.lattice(0).init_equilibrium(rho, u)
+    b.step(0)
+    assert b.lattice(0).t == 0
+    assert np.array_equal(b.lattice(0).populations().cpu().numpy(), before)
