@@ -198,11 +198,21 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
     const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
     bool anybad = act[0] && (bad & 1u);
     if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
-    // odd step, tile away from every row end and boundary row / plane: the
-    // destination (i, x + e_i) is a fixed offset from the node, no wrap, no wall
-    const bool inner = ODD && x0 > 0 && x0 + XT < G.nx && y > 0 && y < G.ny - 1 &&
-                       (L::D == 2 || (z > 0 && z < G.nz - 1));
-    const long long zstride = (long long)G.ny * G.pitch;
+    // odd step: destination row deltas (elements) for e_y = +1 / -1 and
+    // e_z = +1 / -1, with the periodic wrap folded in; kWall marks a wall
+    constexpr long long kWall = -(1LL << 62);
+    const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
+    long long yp = 0, ym = 0, zp = 0, zm = 0;
+    bool xedge = false;  // the tile holds a row end (x wrap or x wall)
+    if constexpr (ODD) {
+      yp = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kWall);
+      ym = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kWall);
+      if (L::D == 3) {
+        zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
+        zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
+      }
+      xedge = x0 == 0 || x0 + XT >= G.nx;
+    }
     R out[NPT];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -223,35 +233,13 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
           for (int n = 0; n < NPT; ++n)
             if (act[n]) op[jn[n]] = S::enc(out[n]);
         }
-      } else if (inner) {
-        T* op = buf + i * G.plane + own + L::cz(i) * zstride + L::cy(i) * G.pitch + L::cx(i) + x0;
-        bool done = false;
-        if constexpr (ADJ) {
-          if (L::cx(i) == 0) {
-            if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(out[0], out[NPT - 1]);
-            else if (act[0]) op[jn[0]] = S::enc(out[0]);
-            done = true;
-          }
-        }
-        if (!done) {
-#pragma unroll
-          for (int n = 0; n < NPT; ++n)
-            if (act[n]) op[jn[n]] = S::enc(out[n]);
-        }
       } else {
         // odd: f*_i(x) into slot (i, x + e_i), or (ibar, x) beyond a wall
         const int ex = L::cx(i);
-        int yd = y + L::cy(i), zd = z + L::cz(i);
-        bool rwall = false;
-        if (yd < 0 || yd >= G.ny) {
-          if (G.per[1]) yd = yd < 0 ? yd + G.ny : yd - G.ny;
-          else rwall = true;
-        }
-        if (zd < 0 || zd >= G.nz) {
-          if (G.per[2]) zd = zd < 0 ? zd + G.nz : zd - G.nz;
-          else rwall = true;
-        }
-        T* rowd = buf + i * G.plane + ((long long)zd * G.ny + yd) * G.pitch;
+        const long long dy = L::cy(i) == 1 ? yp : (L::cy(i) == -1 ? ym : 0);
+        const long long dz = L::cz(i) == 1 ? zp : (L::cz(i) == -1 ? zm : 0);
+        const bool rwall = dy == kWall || dz == kWall;
+        T* rowd = buf + i * G.plane + own + (rwall ? 0 : dy + dz);
         T* rowo = buf + L::opp(i) * G.plane + own;
         bool done = false;
         if constexpr (ADJ) {
@@ -264,18 +252,25 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
           }
         }
         if (!done) {
+          if (!xedge && !rwall) {
+            // away from the row ends: a fixed shift
 #pragma unroll
-          for (int n = 0; n < NPT; ++n) {
-            if (!act[n]) continue;
-            const int x = x0 + jn[n];
-            int xd = x + ex;
-            bool wl = rwall;
-            if (xd < 0 || xd >= G.nx) {
-              if (G.per[0]) xd = xd < 0 ? xd + G.nx : xd - G.nx;
-              else wl = true;
+            for (int n = 0; n < NPT; ++n)
+              if (act[n]) rowd[x0 + jn[n] + ex] = S::enc(out[n]);
+          } else {
+#pragma unroll
+            for (int n = 0; n < NPT; ++n) {
+              if (!act[n]) continue;
+              const int x = x0 + jn[n];
+              int xd = x + ex;
+              bool wl = rwall;
+              if (xd < 0 || xd >= G.nx) {
+                if (G.per[0]) xd = xd < 0 ? xd + G.nx : xd - G.nx;
+                else wl = true;
+              }
+              if (wl) rowo[x] = S::enc(out[n]);
+              else rowd[xd] = S::enc(out[n]);
             }
-            if (wl) rowo[x] = S::enc(out[n]);
-            else rowd[xd] = S::enc(out[n]);
           }
         }
       }
