@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
     constexpr long long kWall = -(1LL << 62);
     const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
     long long yp = 0, ym = 0, zp = 0, zm = 0;
-    bool xedge = false;  // the tile holds a row end (x wrap or x wall)
+    bool xedge = false;  // this thread holds a row end (x wrap or x wall)
     if constexpr (ODD) {
       yp = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kWall);
       ym = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kWall);
@@ -211,7 +211,13 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
         zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
         zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
       }
-      xedge = x0 == 0 || x0 + XT >= G.nx;
+      // only a thread that owns the row's first or last node needs the
+      // per-node wrap / wall test
+#pragma unroll
+      for (int n = 0; n < NPT; ++n) {
+        const int x = x0 + jn[n];
+        xedge |= act[n] && (x == 0 || x == G.nx - 1);
+      }
     }
     R out[NPT];
 #pragma unroll
