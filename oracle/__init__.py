@@ -75,6 +75,9 @@ def _load():
         lib.oracle_l2.restype = ctypes.c_double
         lib.oracle_hermite_contraction.argtypes = [ctypes.c_int, dp, dp, dp]
         lib.oracle_hermite_ranks.argtypes = [ctypes.c_int, ip, ip]
+        lib.oracle_step_open.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_momentum_exchange.argtypes = [pp, dp, dp]
         _lib = lib
     return _lib
 
@@ -245,6 +248,33 @@ def step(p: Params, f: np.ndarray, nsteps: int, nthreads: int = 1) -> np.ndarray
     if rc:
         raise RuntimeError(f"oracle_step failed: {rc}")
     return g
+
+
+def step_open(p: Params, f: np.ndarray, nsteps: int, u_in: float, rho_out: float,
+              rho_w: float = 1.0, nthreads: int = 1) -> np.ndarray:
+    """As step, with the open boundaries of Sec. 3.4 on D2Q9 (x non-periodic):
+    moving-wall bounce-back inlet at the left (velocity u_in, wall density
+    rho_w) and a Zou-He constant-density outlet (rho_out) at x = nx - 1."""
+    lib = _load()
+    g = np.array(f, dtype=np.float64, order="C", copy=True).reshape((p.Q,) + p.shape)
+    cp = p.c()
+    rc = lib.oracle_step_open(ctypes.byref(cp), float(u_in), float(rho_w), float(rho_out), _dp(g),
+                              int(nsteps), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle_step_open failed: {rc}")
+    return g
+
+
+def momentum_exchange(p: Params, f: np.ndarray) -> np.ndarray:
+    """Force on the solid nodes by momentum exchange (Sec. 3.4) for the
+    pre-collision state f: sum over fluid-to-solid links of 2 e_i f*_i."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(3)
+    cp = p.c()
+    if lib.oracle_momentum_exchange(ctypes.byref(cp), _dp(f), _dp(out)):
+        raise RuntimeError("oracle_momentum_exchange failed")
+    return out
 
 
 def macros(p: Params, f: np.ndarray):

@@ -536,6 +536,163 @@ int oracle_step(const or_params* p, double* f, int nsteps, int nthreads) {
   return 0;
 }
 
+/* ------------------------------------------------ open boundaries (Sec. 3.4)
+ * The square-cylinder benchmark of Sec. 3.4 on D2Q9: the left boundary imposes
+ * the uniform velocity u_in by halfway bounce-back from a wall moving with
+ * (u_in, 0), half a spacing left of x = 0:
+ *   f_ibar(x, t+1) = f*_i(x, t) - 2 w_i rho_w (e_i . u_w) / cs^2
+ * for every population f*_i leaving through it; the right boundary is a
+ * constant-pressure outlet by the Zou-He scheme at the nodes x = nx - 1: after
+ * streaming, the three populations that would enter from outside (e_x = -1) are
+ * set so that the node has density rho_out and zero transverse velocity,
+ *   u_x = (sum_{e_x = 0} f + 2 sum_{e_x = +1} f) / rho_out - 1,
+ *   f_i = f_ibar + 2 w_i rho_out (e_i . u) / cs^2 - (e_iy / 2)(f_{+y} - f_{-y}),
+ * which also keeps the non-equilibrium part of the normal pair antisymmetric.
+ * y (and z) follow p->periodic; x must be non-periodic.  Plain and node by node:
+ * collide every fluid node, push-stream as oracle_step, then the outlet. */
+static int zou_he_outlet(const or_lattice* L, double rho_out, double* f /* Q values */) {
+  double s0 = 0.0, sp = 0.0, fyp = 0.0, fym = 0.0;
+  for (int i = 0; i < L->Q; ++i) {
+    if (L->e[i][0] == 0) s0 += f[i];
+    if (L->e[i][0] == 1) sp += f[i];
+    if (L->e[i][0] == 0 && L->e[i][1] == 1) fyp = f[i];
+    if (L->e[i][0] == 0 && L->e[i][1] == -1) fym = f[i];
+  }
+  const double ux = (s0 + 2.0 * sp) / rho_out - 1.0;
+  for (int i = 0; i < L->Q; ++i) {
+    if (L->e[i][0] != -1) continue;
+    const double eu = L->e[i][0] * ux;
+    f[i] = f[L->opp[i]] + 2.0 * L->w[i] * rho_out * eu / OR_CS2 - 0.5 * L->e[i][1] * (fyp - fym);
+  }
+  return 0;
+}
+
+int oracle_step_open(const or_params* p, double u_in, double rho_w, double rho_out, double* f,
+                     int nsteps, int nthreads) {
+  or_lattice L;
+  int rc = build_lattice(p->lattice, &L);
+  if (rc) return rc;
+  if (p->lattice != OR_D2Q9 || p->periodic[0] || p->nx < 2 || !(rho_out > 0.0)) return -4;
+  const int Q = L.Q;
+  const long nx = p->nx, ny = p->ny, nz = p->nz;
+  const size_t N = nnodes(p);
+  double* fs = (double*)malloc(sizeof(double) * Q * N);
+  double* fn = (double*)malloc(sizeof(double) * Q * N);
+  if (!fs || !fn) {
+    free(fs);
+    free(fn);
+    return -3;
+  }
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  for (int s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < (long)N; ++n) {
+      double fl[OR_MAXQ], fo[OR_MAXQ];
+      if (p->solid && p->solid[n]) {
+        for (int i = 0; i < Q; ++i) fs[i * N + n] = f[i * N + n];
+        continue;
+      }
+      for (int i = 0; i < Q; ++i) fl[i] = f[i * N + n];
+      collide_node(&L, p, fl, fo);
+      for (int i = 0; i < Q; ++i) fs[i * N + n] = fo[i];
+    }
+    memcpy(fn, f, sizeof(double) * Q * N);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < (long)N; ++n) {
+      if (p->solid && p->solid[n]) continue;
+      const long x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+      for (int i = 0; i < Q; ++i) {
+        long d[3] = {x + L.e[i][0], y + L.e[i][1], z + L.e[i][2]};
+        const long ext[3] = {nx, ny, nz};
+        int bounce = 0, inlet = 0;
+        for (int a = 0; a < 3; ++a) {
+          if (d[a] < 0 || d[a] >= ext[a]) {
+            if (p->periodic[a]) {
+              d[a] = (d[a] + ext[a]) % ext[a];
+            } else {
+              bounce = 1;
+              if (a == 0 && d[0] < 0) inlet = 1;
+            }
+          }
+        }
+        size_t m = 0;
+        if (!bounce) {
+          m = (size_t)(d[2] * ny + d[1]) * nx + d[0];
+          if (p->solid && p->solid[m]) bounce = 1;
+        }
+        if (bounce) {
+          double v = fs[i * N + n];
+          if (inlet) v -= 2.0 * L.w[i] * rho_w * (L.e[i][0] * u_in) / OR_CS2; /* moving wall */
+          fn[L.opp[i] * N + n] = v;
+        } else {
+          fn[i * N + m] = fs[i * N + n];
+        }
+      }
+    }
+    /* outlet: the populations entering from outside, by Zou-He */
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < ny * nz; ++r) {
+      const size_t n = (size_t)r * nx + (nx - 1);
+      if (p->solid && p->solid[n]) continue;
+      double fl[OR_MAXQ];
+      for (int i = 0; i < Q; ++i) fl[i] = fn[i * N + n];
+      zou_he_outlet(&L, rho_out, fl);
+      for (int i = 0; i < Q; ++i) fn[i * N + n] = fl[i];
+    }
+    memcpy(f, fn, sizeof(double) * Q * N);
+  }
+  free(fs);
+  free(fn);
+  return 0;
+}
+
+/* Force on the solid nodes by momentum exchange (Sec. 3.4): with halfway
+ * bounce-back from resting solid nodes, every link from a fluid node x_f to a
+ * solid neighbour x_f + e_i returns f*_i(x_f) as f_ibar(x_f), so the link
+ * transfers 2 e_i f*_i(x_f, t); f*(t) is the collision of the given
+ * pre-collision state f(t).  out[3]: the force summed over all such links. */
+int oracle_momentum_exchange(const or_params* p, const double* f, double* out) {
+  or_lattice L;
+  int rc = build_lattice(p->lattice, &L);
+  if (rc) return rc;
+  const long nx = p->nx, ny = p->ny, nz = p->nz;
+  const size_t N = nnodes(p);
+  out[0] = out[1] = out[2] = 0.0;
+  if (!p->solid) return 0;
+  for (size_t n = 0; n < N; ++n) {
+    if (p->solid[n]) continue;
+    const long x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    int near = 0;
+    size_t nb[OR_MAXQ];
+    for (int i = 0; i < L.Q; ++i) {
+      long d[3] = {x + L.e[i][0], y + L.e[i][1], z + L.e[i][2]};
+      const long ext[3] = {nx, ny, nz};
+      int out_of = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (d[a] < 0 || d[a] >= ext[a]) {
+          if (p->periodic[a]) d[a] = (d[a] + ext[a]) % ext[a];
+          else out_of = 1;
+        }
+      }
+      nb[i] = out_of ? (size_t)-1 : (size_t)(d[2] * ny + d[1]) * nx + d[0];
+      if (!out_of && p->solid[nb[i]]) near = 1;
+    }
+    if (!near) continue;
+    double fl[OR_MAXQ], fo[OR_MAXQ];
+    for (int i = 0; i < L.Q; ++i) fl[i] = f[i * N + n];
+    collide_node(&L, p, fl, fo);
+    for (int i = 0; i < L.Q; ++i) {
+      if (nb[i] == (size_t)-1 || !p->solid[nb[i]]) continue;
+      for (int a = 0; a < 3; ++a) out[a] += 2.0 * L.e[i][a] * fo[i];
+    }
+  }
+  return 0;
+}
+
 /* Density and half-force velocity (Eq. macro) of the pre-collision state. */
 int oracle_macros(const or_params* p, const double* f, double* rho, double* u) {
   or_lattice L;
