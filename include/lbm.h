@@ -180,6 +180,27 @@ int lbm_diagnostics(lbm_ctx* ctx, double out[8]);
  * Synchronises. */
 int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
 
+/* Open boundaries of the square-cylinder benchmark (Sec. 3.4), D2Q9 with the A/B
+ * layout and a non-periodic x axis: the left boundary imposes the uniform
+ * velocity (u_in, 0) by halfway bounce-back from a wall moving with it (the wall
+ * half a spacing left of x = 0, density rho0), the right boundary is a
+ * constant-pressure outlet by the Zou-He scheme (density rho_out and zero
+ * transverse velocity at the nodes x = nx - 1).  The other axes keep their
+ * periodic / wall settings.  rho_out <= 0 turns them off.  While on, lbm_step
+ * runs a one-node-per-thread kernel that applies them (the variant is ignored)
+ * and lbm_macros, lbm_get_populations and lbm_diagnostics report the state with
+ * them applied.  LBM_ERR_UNSUPPORTED for D3Q19 or AA, LBM_ERR_ARG for a periodic
+ * x axis, nx < 2 or |u_in| >= 1. */
+int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
+
+/* Force on the solid nodes by momentum exchange (Sec. 3.4), FP64, into out[3]:
+ * with halfway bounce-back from resting solids every link from a fluid node to
+ * a solid neighbour transfers 2 e_i f*_i, f* the collision of the current state
+ * (the force of the next streaming step).  Neighbours beyond a non-periodic
+ * edge are walls and not counted.  The drag coefficient of Sec. 3.4 is
+ * C_d = 2 out[0] / (rho0 u_c^2 D).  Synchronises. */
+int lbm_momentum_exchange(lbm_ctx* ctx, double out[3]);
+
 /* Synchronises the stream and reports LBM_ERR_DIVERGED if any update since the
  * last lbm_init_equilibrium / lbm_set_populations met NaN/Inf, rho <= 0 or
  * |u| > 1; *first_step (may be NULL) receives the earliest such step or -1. */

@@ -180,6 +180,7 @@ struct lbm_ctx {
   std::vector<Variant> vars;
   int var = 0;
   int sms = 0;
+  OpenBC open{};  // open boundaries of the square-cylinder benchmark (off by default)
   long long wait_ns = 2000000000LL;
   int extra_tx = 0;
 };
@@ -198,11 +199,13 @@ AuxLaunch aux_of(lbm_ctx* c) {
   a.layout = c->pl.p.layout;
   a.parity = (int)(c->t & 1);
   a.stream = c->stream;
+  a.open = c->open;
   return a;
 }
 
 StepLaunch step_of(lbm_ctx* c, const Variant& v) {
   StepLaunch s{};
+  s.open = c->open;
   s.g = c->pl.g;
   s.collision = c->pl.kernel_collision;
   s.force = c->pl.force;
@@ -507,6 +510,50 @@ int lbm_velocity_l2(lbm_ctx* c, const double* u_ref, double* out) {
   int rc = run_diag(c, u_ref, r);
   if (rc) return rc;
   *out = r[1] > 0.0 ? sqrt(r[0] / r[1]) : (r[0] > 0.0 ? INFINITY : 0.0);
+  return LBM_OK;
+}
+
+int lbm_set_open_boundaries(lbm_ctx* c, double u_in, double rho_out) {
+  CHECK_CTX(c);
+  if (c->view) return fail(LBM_ERR_STATE, "batch views take no open boundaries");
+  if (!(rho_out > 0.0)) {  // off
+    c->open = OpenBC{};
+    return LBM_OK;
+  }
+  if (c->pl.p.lattice != LBM_D2Q9 || c->pl.p.layout != LBM_LAYOUT_AB)
+    return fail(LBM_ERR_UNSUPPORTED, "open boundaries: D2Q9 with the A/B layout");
+  if (c->pl.g.per[0] || c->pl.p.nx < 2)
+    return fail(LBM_ERR_ARG, "open boundaries need a non-periodic x axis with nx >= 2");
+  if (!(fabs(u_in) < 1.0)) return fail(LBM_ERR_ARG, "|u_in| must be < 1");
+  c->open.on = 1;
+  c->open.u_in = u_in;
+  c->open.rho_out = rho_out;
+  return LBM_OK;
+}
+
+int lbm_momentum_exchange(lbm_ctx* c, double out[3]) {
+  CHECK_CTX(c);
+  if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+  double* partials = reinterpret_cast<double*>(c->scratch + kPartialOffset);
+  double* res = reinterpret_cast<double*>(c->scratch + kResultOffset);
+  int dev_sms = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+  long long blocks = (long long)c->pl.p.ny * c->pl.p.nz;
+  const long long cap = dev_sms > 0 ? 8LL * dev_sms : 1024;
+  if (blocks > cap) blocks = cap;
+  if (blocks > kMaxPartials) blocks = kMaxPartials;
+  cudaError_t e = c->ops->momentum(aux_of(c), c->pl.kernel_collision, c->pl.coef, partials,
+                                   (int)blocks, res);
+  c->launches += 2;
+  int rc = cuda_check(e, "momentum exchange");
+  if (rc) return rc;
+  double r[8];
+  rc = cuda_check(cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, c->stream),
+                  "copy force");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  if (rc) return rc;
+  for (int k = 0; k < 3; ++k) out[k] = r[k];
   return LBM_OK;
 }
 

@@ -24,7 +24,16 @@ struct Variant {
   int stages;  // kind 1: shared-memory ring depth
 };
 
+// Open boundaries of the square-cylinder benchmark (D2Q9, A/B, x non-periodic):
+// a wall moving with (u_in, 0) half a spacing left of x = 0, and a Zou-He
+// constant-density outlet (rho_out) at x = nx - 1.
+struct OpenBC {
+  int on;
+  double u_in, rho_out;
+};
+
 struct StepLaunch {
+  OpenBC open;
   GeoH g;
   int collision;  // 0 TRT, 1 TRT-RLB, 2 P-TRT (BGK / RLB mapped by the caller)
   bool force;     // any force component non-zero
@@ -45,6 +54,7 @@ struct StepLaunch {
 };
 
 struct AuxLaunch {
+  OpenBC open;
   GeoH g;
   double rho0, F[3];
   void* pop;            // buffer holding the current state
@@ -102,6 +112,10 @@ struct Ops {
   // (blocks <= rows), the eight sums in out[8] (mass, momentum, kinetic energy,
   // enstrophy, flag, 0)
   cudaError_t (*diag)(const AuxLaunch&, void* fields, double* partials, int blocks, double* out);
+  // force on the solid nodes by momentum exchange (sum over fluid-to-solid links
+  // of 2 e_i f*_i), partials [blocks][8] (slots 0..2), out[8] (slots 0..2)
+  cudaError_t (*momentum)(const AuxLaunch&, int collision, const CoefV<double>& c, double* partials,
+                          int blocks, double* out);
   // persistent batched kernel (cooperative launch) and its occupancy
   cudaError_t (*batch)(const BatchLaunch&);
   int (*batch_blocks_per_sm)(int collision, int threads);

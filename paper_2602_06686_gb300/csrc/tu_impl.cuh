@@ -72,6 +72,63 @@ struct RowNode {
   }
 };
 
+// Open boundaries of the square-cylinder benchmark (Sec. 3.4, D2Q9), applied
+// to the shifted pre-collision populations g of node x as gathered with x
+// non-periodic (a population from beyond either x edge then holds the node's
+// own opposite slot):
+//   inlet  (x = 0): bounce-back from a wall moving with (u_in, 0) adds
+//          6 w_i rho0 u_in to every population with e_x = +1;
+//   outlet (x = nx - 1): Zou-He, density rho_out and zero transverse velocity:
+//          u_x = (sum_{e_x=0} f + 2 sum_{e_x=+1} f) / rho_out - 1 and, for e_x = -1,
+//          f_i = f_ibar + 6 w_i rho_out e_x u_x - (e_y / 2)(f_{+y} - f_{-y}).
+// In shifted variables the rest weights cancel: sum_{e_x=0} w + 2 sum_{e_x=+1} w = 1.
+template <class L, typename R>
+__device__ __forceinline__ void open_fix(int x, int nx, R (&g)[L::Q], R rho0, R u_in, R rho_out) {
+  if (x == 0) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      if (L::cx(i) == 1) g[i] += R(6.0 * L::w(i)) * rho0 * u_in;
+  }
+  if (x == nx - 1) {
+    R s0 = R(0), sp = R(0), gyp = R(0), gym = R(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::cx(i) == 0) s0 += g[i];
+      if (L::cx(i) == 1) sp += g[i];
+      if (L::cx(i) == 0 && L::cy(i) == 1 && L::cz(i) == 0) gyp = g[i];
+      if (L::cx(i) == 0 && L::cy(i) == -1 && L::cz(i) == 0) gym = g[i];
+    }
+    const R ux = (s0 + R(2) * sp + rho0 - rho_out) / rho_out;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      if (L::cx(i) == -1)
+        g[i] = g[L::opp(i)] - R(6.0 * L::w(i)) * rho_out * ux - R(0.5 * L::cy(i)) * (gyp - gym);
+  }
+}
+
+// One fused update with the open boundaries (A/B layout, one node per thread,
+// grid of (row, x block) as the helper kernels).
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R> a,
+                                                   typename S::R u_in, typename S::R rho_out) {
+  using R = typename S::R;
+  using T = typename S::T;
+  const Geo& G = a.g;
+  const RowNode q(G);
+  if (!q.valid || (a.mask && a.mask[q.n])) return;
+  const T* __restrict__ src = static_cast<const T*>(a.src);
+  T* __restrict__ dst = static_cast<T*>(a.dst);
+  R g[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) g[i] = S::dec(src[ab_slot<L>(G, a.mask, q.x, q.y, q.z, i)]);
+  open_fix<L, R>(q.x, G.nx, g, a.c.rho0, u_in, rho_out);
+  const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
+  const long long own = ((long long)q.z * G.ny + q.y) * G.pitch + q.x;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) dst[i * G.plane + own] = S::enc(g[i]);
+  record_bad(a.flag, a.step, bad);
+}
+
 template <class L, class S>
 __global__ void __launch_bounds__(256) k_init_eq(Geo G, const uint8_t* mask, int layout, int parity,
                                                  typename S::T* pop, const double* rho,
@@ -106,7 +163,7 @@ template <class L, class S>
 __global__ void __launch_bounds__(256) k_get(Geo G, const uint8_t* mask, int layout, int parity,
                                              const typename S::T* pop, double rho0, double Fx,
                                              double Fy, double Fz, int mode, double* out0,
-                                             double* out1) {
+                                             double* out1, OpenBC open) {
   const long long N = (long long)G.nx * G.ny * G.nz;
   const RowNode q(G);
   if (!q.valid) return;
@@ -116,6 +173,7 @@ __global__ void __launch_bounds__(256) k_get(Geo G, const uint8_t* mask, int lay
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
     g[i] = solid ? 0.0 : double(S::dec(pop[state_slot<L>(G, mask, layout, parity, q.x, q.y, q.z, i)]));
+  if (open.on && !solid) open_fix<L, double>(q.x, G.nx, g, rho0, open.u_in, open.rho_out);
   if (mode == 0) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) out0[i * N + n] = g[i] + L::w(i) * rho0;
@@ -202,7 +260,8 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
                                                      int parity, const typename S::T* pop,
                                                      double rho0d, typename S::R Fhx,
                                                      typename S::R Fhy, typename S::R Fhz,
-                                                     typename S::R* fld, double* partials) {
+                                                     typename S::R* fld, double* partials,
+                                                     OpenBC open) {
   using R = typename S::R;
   const long long N = (long long)G.nx * G.ny * G.nz;
   const R rho0 = R(rho0d);
@@ -238,7 +297,7 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
         for (int a = 0; a < L::D; ++a) fld[(1 + a) * N + n] = R(0);
         continue;
       }
-      R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+      R gq[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         R g;
@@ -261,6 +320,13 @@ __global__ void __launch_bounds__(256) k_diag_fields(Geo G, const uint8_t* mask,
         } else {
           g = S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]);
         }
+        gq[i] = g;
+      }
+      if (open.on) open_fix<L, R>(x, G.nx, gq, rho0, R(open.u_in), R(open.rho_out));
+      R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const R g = gq[i];
         drho += g;
         if (L::cx(i) == 1) jx += g;
         if (L::cx(i) == -1) jx -= g;
@@ -346,6 +412,59 @@ __global__ void __launch_bounds__(256) k_diag_enstrophy(Geo G, const uint8_t* ma
   }
   const double acc[1] = {se.value()};
   block_partials<1>(acc, partials, 5);
+}
+
+// Force on the solid nodes by momentum exchange (Sec. 3.4): with halfway
+// bounce-back from resting solid nodes every link from a fluid node x_f to a
+// solid neighbour x_f + e_i returns f*_i(x_f) as f_ibar(x_f), so it transfers
+// 2 e_i f*_i(x_f); f* is the collision of the current pre-collision state (the
+// force of the coming streaming step).  Neighbours beyond a non-periodic edge
+// are walls, not part of the body.  Partial sums per block into slots 0..2.
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(256) k_momentum(Geo G, const uint8_t* mask, int layout,
+                                                  int parity, const typename S::T* pop,
+                                                  const CoefV<typename S::R> c, OpenBC open,
+                                                  double* partials) {
+  using R = typename S::R;
+  int r0, r1;
+  block_rows(G, r0, r1);
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  int y = r0 % G.ny, z = r0 / G.ny;
+  for (int r = r0; r < r1; ++r) {
+    for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+      const long long n = (long long)r * G.nx + x;
+      if (!mask || mask[n]) continue;
+      unsigned links = 0u;
+#pragma unroll
+      for (int i = 1; i < L::Q; ++i) {
+        bool out = false;
+        const int xd = aa_wrap(x + L::cx(i), G.nx, G.per[0], out);
+        const int yd = aa_wrap(y + L::cy(i), G.ny, G.per[1], out);
+        const int zd = aa_wrap(z + L::cz(i), G.nz, G.per[2], out);
+        if (!out && mask[((long long)zd * G.ny + yd) * G.nx + xd]) links |= 1u << i;
+      }
+      if (!links) continue;
+      R g[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) g[i] = S::dec(pop[state_slot<L>(G, mask, layout, parity, x, y, z, i)]);
+      if (open.on) open_fix<L, R>(x, G.nx, g, c.rho0, R(open.u_in), R(open.rho_out));
+      collide_v<L, COLL, true, R>(g, c);
+#pragma unroll
+      for (int i = 1; i < L::Q; ++i) {
+        if (!(links & (1u << i))) continue;
+        const double fs = 2.0 * (double(g[i]) + L::w(i) * double(c.rho0));
+        fx += L::cx(i) * fs;
+        fy += L::cy(i) * fs;
+        fz += L::cz(i) * fs;
+      }
+    }
+    if (++y == G.ny) {
+      y = 0;
+      ++z;
+    }
+  }
+  const double acc[8] = {fx, fy, fz, 0.0, 0.0, 0.0, 0.0, 0.0};
+  block_partials<8>(acc, partials, 0);
 }
 
 template <class L, class S>
@@ -511,7 +630,53 @@ struct TU {
     return cudaErrorInvalidValue;
   }
 
+  template <int COLL>
+  static cudaError_t go_open(const StepLaunch& s) {
+    const dim3 grid((unsigned)((long long)s.g.ny * s.g.nz), (unsigned)((s.g.nx + 255) / 256));
+    k_step_open<L, COLL, S><<<grid, 256, 0, s.stream>>>(args(s), R(s.open.u_in), R(s.open.rho_out));
+    return cudaGetLastError();
+  }
+  static cudaError_t step_open(const StepLaunch& s) {
+    if (s.layout != 0) return cudaErrorInvalidValue;
+    switch (s.collision) {
+      case C_TRT:
+        return go_open<C_TRT>(s);
+      case C_TRT_RLB:
+        return go_open<C_TRT_RLB>(s);
+      case C_P_TRT:
+        return go_open<C_P_TRT>(s);
+    }
+    return cudaErrorInvalidValue;
+  }
+
+  template <int COLL>
+  static cudaError_t go_momentum(const AuxLaunch& a, const CoefV<double>& c, double* partials,
+                                 int blocks) {
+    k_momentum<L, COLL, S><<<blocks, 256, 0, a.stream>>>(geo(a.g), a.mask, a.layout, a.parity,
+                                                         static_cast<const T*>(a.pop),
+                                                         coef_cast<R>(c), a.open, partials);
+    return cudaGetLastError();
+  }
+  static cudaError_t momentum(const AuxLaunch& a, int collision, const CoefV<double>& c,
+                              double* partials, int blocks, double* out) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (collision) {
+      case C_TRT:
+        e = go_momentum<C_TRT>(a, c, partials, blocks);
+        break;
+      case C_TRT_RLB:
+        e = go_momentum<C_TRT_RLB>(a, c, partials, blocks);
+        break;
+      case C_P_TRT:
+        e = go_momentum<C_P_TRT>(a, c, partials, blocks);
+        break;
+    }
+    if (e != cudaSuccess) return e;
+    return reduce_partials(partials, blocks, out, a.stream);
+  }
+
   static cudaError_t step(const StepLaunch& s) {
+    if (s.open.on) return step_open(s);
     if (s.v.kind == 1) return step_tma(s);
     switch (s.v.nv) {
       case 1:
@@ -539,7 +704,7 @@ struct TU {
     k_diag_fields<L, S><<<blocks, 256, 0, a.stream>>>(G, a.mask, a.layout, a.parity,
                                                       static_cast<const T*>(a.pop), a.rho0,
                                                       R(0.5 * a.F[0]), R(0.5 * a.F[1]),
-                                                      R(0.5 * a.F[2]), fld, partials);
+                                                      R(0.5 * a.F[2]), fld, partials, a.open);
     k_diag_enstrophy<R, L::D><<<blocks, 256, 0, a.stream>>>(G, a.mask, fld, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -559,13 +724,13 @@ struct TU {
   static cudaError_t get_pop(const AuxLaunch& a, double* f) {
     k_get<L, S><<<aux_grid(a.g), 256, 0, a.stream>>>(geo(a.g), a.mask, a.layout, a.parity,
                                                      static_cast<const T*>(a.pop), a.rho0,
-                                                     a.F[0], a.F[1], a.F[2], 0, f, nullptr);
+                                                     a.F[0], a.F[1], a.F[2], 0, f, nullptr, a.open);
     return cudaGetLastError();
   }
   static cudaError_t macros(const AuxLaunch& a, double* rho, double* u) {
     k_get<L, S><<<aux_grid(a.g), 256, 0, a.stream>>>(geo(a.g), a.mask, a.layout, a.parity,
                                                      static_cast<const T*>(a.pop), a.rho0,
-                                                     a.F[0], a.F[1], a.F[2], 1, rho, u);
+                                                     a.F[0], a.F[1], a.F[2], 1, rho, u, a.open);
     return cudaGetLastError();
   }
 
@@ -708,6 +873,7 @@ struct TU {
       r.get_pop = &get_pop;
       r.macros = &macros;
       r.diag = &diag;
+      r.momentum = &momentum;
       r.batch = &batch;
       r.batch_blocks_per_sm = &batch_blocks_per_sm;
       if (kPack) {

@@ -36,6 +36,7 @@ EXPORTED = [
     "lbm_batch_step", "lbm_batch_variant_count", "lbm_batch_variant_name",
     "lbm_batch_set_variant", "lbm_batch_autotune", "lbm_batch_set_barrier",
     "lbm_batch_launches", "lbm_batch_destroy", "lbm_diagnostics_noalloc",
+    "lbm_set_open_boundaries", "lbm_momentum_exchange",
 ]
 
 
@@ -119,6 +120,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_batch_launches": ([vp, ll], ctypes.c_int),
         "lbm_batch_destroy": ([vp], ctypes.c_int),
         "lbm_diagnostics_noalloc": ([pp, vp, vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
+        "lbm_set_open_boundaries": ([vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+        "lbm_momentum_exchange": ([vp, dp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -274,6 +277,18 @@ class Lattice:
         _check(self.lib.lbm_diagnostics(self.ctx, out), "lbm_diagnostics")
         return {"mass": out[0], "momentum": np.array(out[1:4]), "kinetic_energy": out[4],
                 "enstrophy": out[5], "nan_flag": out[6], "step": int(out[7])}
+
+    def set_open_boundaries(self, u_in: float, rho_out: float):
+        """Moving-wall inlet (u_in, 0) at the left, Zou-He outlet (rho_out) at the
+        right (D2Q9, A/B, x non-periodic); rho_out <= 0 turns them off."""
+        _check(self.lib.lbm_set_open_boundaries(self.ctx, float(u_in), float(rho_out)),
+               "lbm_set_open_boundaries")
+
+    def momentum_exchange(self) -> np.ndarray:
+        """Force on the solid nodes by momentum exchange, FP64 (3 components)."""
+        out = (ctypes.c_double * 3)()
+        _check(self.lib.lbm_momentum_exchange(self.ctx, out), "lbm_momentum_exchange")
+        return np.array(out[:])
 
     def velocity_l2(self, u_ref) -> float:
         ur = self._dev64(u_ref, (self.D,) + self.shape)

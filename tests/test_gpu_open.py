@@ -1,0 +1,95 @@
+"""GPU tests of the square-cylinder machinery (Sec. 3.4): the moving-wall inlet
+and Zou-He outlet, and the momentum-exchange force on solid nodes, against the
+FP64 oracle on the same seeded inputs (FP64 to 1e-12 in the populations, FP32
+to 2e-5 in rho and u; the force to 1e-10 in FP64)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_cases import elem_rel, gpu_lattice, oracle_params, scaled_err
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (1, 24, 48)
+
+
+def _solid():
+    s = np.zeros(SHAPE, dtype=np.uint8)
+    s[0, 9:15, 16:22] = 1
+    return s
+
+
+@pytest.mark.parametrize("coll", [O.P_TRT, O.TRT, O.TRT_RLB])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_open_boundaries_match_oracle(coll, storage):
+    solid = _solid()
+    rng = np.random.default_rng(81)
+    rho, u = W.random_macros(SHAPE, 2, rng, umax=0.02)
+    u = u * (solid == 0)
+    per = (0, 1, 1)
+    g = gpu_lattice(O.D2Q9, SHAPE, coll, 0.05, 3 / 16, storage=storage, periodic=per, solid=solid)
+    g.set_open_boundaries(0.03, 0.99)
+    g.init_equilibrium(rho, u)
+    g.step(150)
+    p = oracle_params(O.D2Q9, SHAPE, coll, 0.05, 3 / 16, periodic=per, solid=solid)
+    ref = O.step_open(p, O.init_equilibrium(p, rho, u), 150, u_in=0.03, rho_out=0.99, nthreads=4)
+    if storage == "F64":
+        assert elem_rel(g.populations().cpu().numpy(), ref, solid) < 1e-12
+        f_gpu = g.momentum_exchange()
+        f_ref = O.momentum_exchange(p, ref)
+        assert np.max(np.abs(f_gpu - f_ref)) <= 1e-10 * np.max(np.abs(f_ref))
+    else:
+        r_gpu, u_gpu = (t.cpu().numpy() for t in g.macros())
+        r_ref, u_ref = O.macros(p, ref)
+        fl = solid == 0
+        assert np.max(np.abs(r_gpu - r_ref)[fl] / r_ref[fl]) < 2e-5
+        assert scaled_err(u_gpu, u_ref, solid) < 2e-5
+    assert g.status()[0] == 0
+
+
+def test_momentum_exchange_without_open_boundaries():
+    """Periodic box, body force, resting obstacle: the force matches the oracle's
+    at every checked time (FP64)."""
+    shape = (1, 20, 20)
+    solid = np.zeros(shape, dtype=np.uint8)
+    solid[0, 8:12, 8:12] = 1
+    F = (1e-5, 2e-6, 0.0)
+    g = gpu_lattice(O.D2Q9, shape, O.P_TRT, 0.1, 3 / 16, force=F, solid=solid)
+    p = oracle_params(O.D2Q9, shape, O.P_TRT, 0.1, 3 / 16, force=F, solid=solid)
+    r0, u0 = W.channel_at_rest(shape, 2)
+    g.init_equilibrium(r0, u0)
+    f = O.init_equilibrium(p, r0, u0)
+    for n in (0, 7, 300):
+        if n:
+            g.step(n)
+            f = O.step(p, f, n)
+        got, want = g.momentum_exchange(), O.momentum_exchange(p, f)
+        assert np.max(np.abs(got - want)) <= 1e-10 * max(np.max(np.abs(want)), 1e-30), n
+
+
+def test_open_boundaries_errors_and_switch_off():
+    from paper_2602_06686_gb300 import LBMError
+    g3 = gpu_lattice(O.D3Q19, (4, 4, 8), O.P_TRT, 0.05, 0.25, periodic=(0, 1, 1))
+    with pytest.raises(LBMError) as e:
+        g3.set_open_boundaries(0.01, 1.0)
+    assert e.value.code == -5
+    gaa = gpu_lattice(O.D2Q9, SHAPE, O.P_TRT, 0.05, 0.25, periodic=(0, 1, 1), layout="AA")
+    with pytest.raises(LBMError) as e:
+        gaa.set_open_boundaries(0.01, 1.0)
+    assert e.value.code == -5
+    gp = gpu_lattice(O.D2Q9, SHAPE, O.P_TRT, 0.05, 0.25)
+    with pytest.raises(LBMError) as e:
+        gp.set_open_boundaries(0.01, 1.0)
+    assert e.value.code == -1
+    # on, then off: stepping is the plain walled update again
+    rng = np.random.default_rng(82)
+    rho, u = W.random_macros(SHAPE, 2, rng, umax=0.02)
+    a = gpu_lattice(O.D2Q9, SHAPE, O.P_TRT, 0.05, 0.25, periodic=(0, 1, 1))
+    b = gpu_lattice(O.D2Q9, SHAPE, O.P_TRT, 0.05, 0.25, periodic=(0, 1, 1))
+    a.set_open_boundaries(0.02, 1.0)
+    a.set_open_boundaries(0.0, 0.0)
+    for g in (a, b):
+        g.init_equilibrium(rho, u)
+        g.step(9)
+    assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
