@@ -670,6 +670,61 @@ def taylor_green_run(n: int = 384, steps: int = 2000, every: int = 100):
     return out
 
 
+def cylinder_drag(re: float, d: int = 21, lfac: int = 50, storage: str = "F32",
+                  check: int = 5000, tol: float = 1e-6, max_steps: int = 400000,
+                  collision: str = "P_TRT"):
+    """Drag of the square cylinder of Sec. 3.4: side d centred in an (lfac d)^2
+    domain, moving-wall inlet at u_c on the left, Zou-He outlet (rho = 1) on the
+    right, y periodic, Lambda = 3/16, Ma = min(0.1, sqrt(0.1 Re)) (T = Ma^2/Re =
+    0.1 in the low-Re regime of Tab. 3), nu = u_c d / Re.  Starts from the
+    uniform stream, steps until C_d = 2 F_x / (rho0 u_c^2 d) changes by less
+    than tol (relative) over `check` steps.  Returns C_d, C_d,mu = C_d Re, the
+    steps taken and, for 2 <= Re <= 40, Sen's C_d = 0.7496 + 10.5767 Re^-0.66."""
+    import torch
+    import workloads as W
+    from paper_2602_06686_gb300 import Lattice
+    n = lfac * d
+    ma = min(0.1, math.sqrt(0.1 * re))
+    uc = ma / math.sqrt(3.0)
+    nu = uc * d / re
+    solid = W.square_cylinder_mask(n, n, d)
+    g = Lattice(lattice="D2Q9", nx=n, ny=n, nu=nu, Lambda=3 / 16, collision=collision,
+                storage=storage, periodic=(0, 1, 1), solid=solid)
+    g.set_open_boundaries(uc, 1.0)
+    rho = np.ones((1, n, n))
+    u = np.zeros((2, 1, n, n))
+    u[0] = uc * (solid == 0)
+    g.init_equilibrium(rho, u)
+    cd_prev, steps, cd = None, 0, float("nan")
+    t0 = time.perf_counter()
+    while steps < max_steps:
+        g.step(check)
+        steps += check
+        cd = 2.0 * g.momentum_exchange()[0] / (uc * uc * d)
+        if cd_prev is not None and abs(cd - cd_prev) <= tol * abs(cd):
+            break
+        cd_prev = cd
+    torch.cuda.synchronize()
+    out = {"re": re, "ma": ma, "tau_plus": 0.5 + 3 * nu, "cd": cd, "cd_mu": cd * re,
+           "steps": steps, "seconds": time.perf_counter() - t0, "diverged": g.status()[0] != 0}
+    if 2 <= re <= 40:
+        out["cd_sen"] = 0.7496 + 10.5767 * re ** -0.66
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_cylinder_study(args):
+    """Square-cylinder drag (Sec. 3.4): C_d,mu at Re = 0.1 (Tab. 3) and C_d at
+    Re = 2..20 against Sen's law, D = 21, L = 50 D."""
+    from paper_2602_06686_gb300 import build
+    build.build()
+    res = {"study": "cylinder", "low_re": [cylinder_drag(0.1, storage=s) for s in ("F32", "F64")],
+           "sen": [cylinder_drag(re) for re in (2.0, 5.0, 10.0, 20.0)]}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_precision_study(args):
     """Full precision study (minutes): channel at nu = 0.1, 0.01, 0.001 (the FP64
     oracle on one column at nu = 0.1), the full-channel throughput per format,
@@ -897,7 +952,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", choices=["precision", "stability"], default=None,
+    ap.add_argument("--study", choices=["precision", "stability", "cylinder"], default=None,
                     help="run the precision study or the critical-Mach stability sweep "
                          "instead of the benchmark")
     ap.add_argument("--cyl-steps", type=int, default=0,
@@ -913,6 +968,8 @@ def main():
         return run_precision_study(args)
     if args.study == "stability":
         return run_stability_study(args)
+    if args.study == "cylinder":
+        return run_cylinder_study(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
