@@ -189,8 +189,10 @@ int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
  * periodic / wall settings.  rho_out <= 0 turns them off.  While on, lbm_step
  * runs a one-node-per-thread kernel that applies them (the variant is ignored)
  * and lbm_macros, lbm_get_populations and lbm_diagnostics report the state with
- * them applied.  LBM_ERR_UNSUPPORTED for D3Q19 or AA, LBM_ERR_ARG for a periodic
- * x axis, nx < 2 or |u_in| >= 1. */
+ * them applied.  A state written directly (lbm_init_equilibrium,
+ * lbm_set_populations, lbm_restore at t = 0) is taken as given: the rules act
+ * from the first streaming on.  LBM_ERR_UNSUPPORTED for D3Q19 or AA,
+ * LBM_ERR_ARG for a periodic x axis, nx < 2 or |u_in| >= 1. */
 int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
 
 /* Force on the solid nodes by momentum exchange (Sec. 3.4), FP64, into out[3]:

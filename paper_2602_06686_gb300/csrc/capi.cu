@@ -181,6 +181,7 @@ struct lbm_ctx {
   int var = 0;
   int sms = 0;
   OpenBC open{};  // open boundaries of the square-cylinder benchmark (off by default)
+  bool fresh = true;  // the state was written directly (not yet streamed)
   long long wait_ns = 2000000000LL;
   int extra_tx = 0;
 };
@@ -200,12 +201,14 @@ AuxLaunch aux_of(lbm_ctx* c) {
   a.parity = (int)(c->t & 1);
   a.stream = c->stream;
   a.open = c->open;
+  a.open.on = c->open.on && !c->fresh;
   return a;
 }
 
 StepLaunch step_of(lbm_ctx* c, const Variant& v) {
   StepLaunch s{};
   s.open = c->open;
+  s.open.fix = c->open.on && !c->fresh;
   s.g = c->pl.g;
   s.collision = c->pl.kernel_collision;
   s.force = c->pl.force;
@@ -275,6 +278,7 @@ int ctx_step(lbm_ctx* c, int n) {
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "stream-collide launch", e);
     if (c->pl.p.layout == LBM_LAYOUT_AB) c->cur ^= 1;
     ++c->t;
+    c->fresh = false;
   }
   return LBM_OK;
 }
@@ -371,6 +375,7 @@ int lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) {
   if (!rho || !u) return fail(LBM_ERR_ARG, "rho and u are required");
   c->cur = 0;
   c->t = 0;
+  c->fresh = true;
   int rc = reset_flag(c);
   if (rc) return rc;
   cudaError_t e = c->ops->init_eq(aux_of(c), rho, u);
@@ -436,6 +441,7 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
   if (!f) return fail(LBM_ERR_ARG, "f is NULL");
   int rc = reset_flag(c);
   if (rc) return rc;
+  c->fresh = true;
   cudaError_t e = c->ops->set_pop(aux_of(c), f);
   ++c->launches;
   return cuda_check(e, "set populations");
@@ -594,6 +600,7 @@ int lbm_restore(lbm_ctx* c, const void* src, size_t bytes, long long t) {
   if (!src || bytes != c->pl.pop_bytes || t < 0) return fail(LBM_ERR_ARG, "bad snapshot");
   c->cur = 0;
   c->t = t;
+  c->fresh = t == 0;
   int rc = reset_flag(c);
   if (rc) return rc;
   return cuda_check(cudaMemcpyAsync(c->pop[0], src, bytes, cudaMemcpyDeviceToDevice, c->stream),

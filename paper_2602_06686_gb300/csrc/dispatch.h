@@ -27,8 +27,12 @@ struct Variant {
 // Open boundaries of the square-cylinder benchmark (D2Q9, A/B, x non-periodic):
 // a wall moving with (u_in, 0) half a spacing left of x = 0, and a Zou-He
 // constant-density outlet (rho_out) at x = nx - 1.
+// `fix` (step launches): apply the boundary rules to the gathered state; off
+// for the first step after the state was written directly (lbm_init_equilibrium,
+// lbm_set_populations), which holds f(t) as given, not a streamed state.
+// For the helper kernels `on` already carries that condition.
 struct OpenBC {
-  int on;
+  int on, fix;
   double u_in, rho_out;
 };
 

@@ -109,7 +109,7 @@ __device__ __forceinline__ void open_fix(int x, int nx, R (&g)[L::Q], R rho0, R 
 // One fused update with the open boundaries (A/B layout, one node per thread,
 // grid of (row, x block) as the helper kernels).
 template <class L, int COLL, class S>
-__global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R> a,
+__global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R> a, int fix,
                                                    typename S::R u_in, typename S::R rho_out) {
   using R = typename S::R;
   using T = typename S::T;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R>
   R g[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) g[i] = S::dec(src[ab_slot<L>(G, a.mask, q.x, q.y, q.z, i)]);
-  open_fix<L, R>(q.x, G.nx, g, a.c.rho0, u_in, rho_out);
+  if (fix) open_fix<L, R>(q.x, G.nx, g, a.c.rho0, u_in, rho_out);
   const bool bad = collide_v<L, COLL, true, R>(g, a.c) != 0u;
   const long long own = ((long long)q.z * G.ny + q.y) * G.pitch + q.x;
 #pragma unroll
@@ -633,7 +633,8 @@ struct TU {
   template <int COLL>
   static cudaError_t go_open(const StepLaunch& s) {
     const dim3 grid((unsigned)((long long)s.g.ny * s.g.nz), (unsigned)((s.g.nx + 255) / 256));
-    k_step_open<L, COLL, S><<<grid, 256, 0, s.stream>>>(args(s), R(s.open.u_in), R(s.open.rho_out));
+    k_step_open<L, COLL, S><<<grid, 256, 0, s.stream>>>(args(s), s.open.fix, R(s.open.u_in),
+                                                        R(s.open.rho_out));
     return cudaGetLastError();
   }
   static cudaError_t step_open(const StepLaunch& s) {
