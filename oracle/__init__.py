@@ -78,6 +78,9 @@ def _load():
         lib.oracle_step_open.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          dp, ctypes.c_int, ctypes.c_int]
         lib.oracle_momentum_exchange.argtypes = [pp, dp, dp]
+        lib.oracle_cubic_flux_gradient.argtypes = [pp, dp, dp]
+        lib.oracle_collide_s2.argtypes = [pp, dp, dp, dp]
+        lib.oracle_step_s2.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -275,6 +278,44 @@ def momentum_exchange(p: Params, f: np.ndarray) -> np.ndarray:
     if lib.oracle_momentum_exchange(ctypes.byref(cp), _dp(f), _dp(out)):
         raise RuntimeError("oracle_momentum_exchange failed")
     return out
+
+
+def cubic_flux_gradient(p: Params, f: np.ndarray) -> np.ndarray:
+    """d_a (rho u_a^3) of the pre-collision state f, shape (D, nz, ny, nx): the
+    non-zero entries of d_g Phi_abg in G_i (Eq. Gi), by central differences,
+    one-sided next to a solid node or a non-periodic edge."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros((p.D,) + p.shape)
+    cp = p.c()
+    if lib.oracle_cubic_flux_gradient(ctypes.byref(cp), _dp(f), _dp(out)):
+        raise RuntimeError("oracle_cubic_flux_gradient failed")
+    return out
+
+
+def collide_s2(p: Params, f: np.ndarray, dphi) -> np.ndarray:
+    """Post-collision populations of one node with the Scheme II source
+    (Eq. source_simple, Eq. Gi); dphi (3, 3) = d_g Phi_abg."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    d = np.ascontiguousarray(np.asarray(dphi, dtype=np.float64).reshape(3, 3))
+    out = np.empty_like(f)
+    cp = p.c()
+    if lib.oracle_collide_s2(ctypes.byref(cp), _dp(f), _dp(d), _dp(out)):
+        raise RuntimeError("oracle_collide_s2 failed")
+    return out
+
+
+def step_s2(p: Params, f: np.ndarray, nsteps: int, nthreads: int = 1) -> np.ndarray:
+    """As step, with the Scheme II source (Eq. source_simple, Eq. Gi) instead of
+    the Guo source; d_g Phi from the pre-collision state of each step."""
+    lib = _load()
+    g = np.array(f, dtype=np.float64, order="C", copy=True).reshape((p.Q,) + p.shape)
+    cp = p.c()
+    rc = lib.oracle_step_s2(ctypes.byref(cp), _dp(g), int(nsteps), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle_step_s2 failed: {rc}")
+    return g
 
 
 def macros(p: Params, f: np.ndarray):

@@ -295,7 +295,13 @@ static void ghost_projection(const or_lattice* L, const double* fneq, double* pg
   }
 }
 
-static void collide_node(const or_lattice* L, const or_params* p, const double* f, double* fs) {
+/* One node's collision.  scheme 1: the Guo source (Eq. source_guo, reading (b));
+ * scheme 2: the simplified projection source of Eq. source_simple,
+ *   S_i = (1 - w+/2) F_i + G_i,
+ *   G_i = -(1 - w+/2) w_i H2_i,ab (d_g Phi_abg) / (6 cs6)          (Eq. Gi)
+ * with dphi[a][b] = d_g Phi_abg given by the caller (a non-local quantity). */
+static void collide_scheme(const or_lattice* L, const or_params* p, const double* f, double* fs,
+                           int scheme, const double (*dphi)[3]) {
   const double cs2 = OR_CS2, cs4 = cs2 * cs2;
   const int Q = L->Q, D = L->D;
   const double* F = p->force;
@@ -366,9 +372,22 @@ static void collide_node(const or_lattice* L, const or_params* p, const double* 
       default:
         R2 = R3 = 0.0;
     }
-    fs[i] = feq[i] + (1.0 - wp) * R2 + (1.0 - wm) * R3 + (1.0 - wp) * R1 +
-            (1.0 - 0.5 * wp) * sguo;
+    if (scheme == 1) {
+      fs[i] = feq[i] + (1.0 - wp) * R2 + (1.0 - wm) * R3 + (1.0 - wp) * R1 +
+              (1.0 - 0.5 * wp) * sguo;
+    } else {
+      double h2d = 0.0; /* H2_i : d_g Phi */
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) h2d += L->H2[i][a][b] * dphi[a][b];
+      const double Gi = -(1.0 - 0.5 * wp) * w * h2d / (6.0 * cs4 * cs2); /* Eq. Gi */
+      fs[i] = feq[i] + (1.0 - wp) * R2 + (1.0 - wm) * R3 + (1.0 - wp) * R1 +
+              (1.0 - 0.5 * wp) * Fi + Gi; /* Eq. source_simple */
+    }
   }
+}
+
+static void collide_node(const or_lattice* L, const or_params* p, const double* f, double* fs) {
+  collide_scheme(L, p, f, fs, 1, NULL);
 }
 
 /* ------------------------------------------------------------- public API */
@@ -468,6 +487,46 @@ int oracle_init_equilibrium(const or_params* p, const double* rho, const double*
   return 0;
 }
 
+/* Push-stream the post-collision fs into f (Sec. 3.3): f*_i(x) moves to
+ * x + e_i, wrapping periodic axes; a population that would enter a solid node
+ * or leave through a non-periodic edge returns to x as f_ibar (halfway
+ * bounce-back).  Solid nodes keep their values.  fn is scratch of f's size. */
+static void push_stream(const or_lattice* L, const or_params* p, double* f, const double* fs,
+                        double* fn) {
+  const int Q = L->Q;
+  const long nx = p->nx, ny = p->ny, nz = p->nz;
+  const size_t N = nnodes(p);
+  memcpy(fn, f, sizeof(double) * Q * N); /* solid nodes keep their values */
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < (long)N; ++n) {
+    if (p->solid && p->solid[n]) continue;
+    const long x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    for (int i = 0; i < Q; ++i) {
+      long d[3] = {x + L->e[i][0], y + L->e[i][1], z + L->e[i][2]};
+      const long ext[3] = {nx, ny, nz};
+      int bounce = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (d[a] < 0 || d[a] >= ext[a]) {
+          if (p->periodic[a])
+            d[a] = (d[a] + ext[a]) % ext[a];
+          else
+            bounce = 1;
+        }
+      }
+      size_t m = 0;
+      if (!bounce) {
+        m = (size_t)(d[2] * ny + d[1]) * nx + d[0];
+        if (p->solid && p->solid[m]) bounce = 1;
+      }
+      if (bounce)
+        fn[L->opp[i] * N + n] = fs[i * N + n];
+      else
+        fn[i * N + m] = fs[i * N + n];
+    }
+  }
+  memcpy(f, fn, sizeof(double) * Q * N);
+}
+
 /* n time steps: collide every fluid node, then push-stream with bounce-back.
  * f is updated in place ([Q][N]); nthreads <= 0 uses the OpenMP default. */
 int oracle_step(const or_params* p, double* f, int nsteps, int nthreads) {
@@ -475,7 +534,6 @@ int oracle_step(const or_params* p, double* f, int nsteps, int nthreads) {
   int rc = build_lattice(p->lattice, &L);
   if (rc) return rc;
   const int Q = L.Q;
-  const long nx = p->nx, ny = p->ny, nz = p->nz;
   const size_t N = nnodes(p);
   double* fs = (double*)malloc(sizeof(double) * Q * N);
   double* fn = (double*)malloc(sizeof(double) * Q * N);
@@ -501,38 +559,155 @@ int oracle_step(const or_params* p, double* f, int nsteps, int nthreads) {
       collide_node(&L, p, fl, fo);
       for (int i = 0; i < Q; ++i) fs[i * N + n] = fo[i];
     }
-    memcpy(fn, f, sizeof(double) * Q * N); /* solid nodes keep their values */
-#pragma omp parallel for schedule(static)
-    for (long n = 0; n < (long)N; ++n) {
-      if (p->solid && p->solid[n]) continue;
-      const long x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
-      for (int i = 0; i < Q; ++i) {
-        long d[3] = {x + L.e[i][0], y + L.e[i][1], z + L.e[i][2]};
-        const long ext[3] = {nx, ny, nz};
-        int bounce = 0;
-        for (int a = 0; a < 3; ++a) {
-          if (d[a] < 0 || d[a] >= ext[a]) {
-            if (p->periodic[a])
-              d[a] = (d[a] + ext[a]) % ext[a];
-            else
-              bounce = 1;
-          }
-        }
-        size_t m = 0;
-        if (!bounce) {
-          m = (size_t)(d[2] * ny + d[1]) * nx + d[0];
-          if (p->solid && p->solid[m]) bounce = 1;
-        }
-        if (bounce)
-          fn[L.opp[i] * N + n] = fs[i * N + n];
-        else
-          fn[i * N + m] = fs[i * N + n];
-      }
-    }
-    memcpy(f, fn, sizeof(double) * Q * N);
+    push_stream(&L, p, f, fs, fn);
   }
   free(fs);
   free(fn);
+  return 0;
+}
+
+/* ------------------------------- Scheme II forcing (Eq. source_simple, Eq. Gi)
+ * The cubic-velocity correction G_i needs d_g Phi_abg, where Phi is zero but
+ * for Phi_aaa = rho u_a^3 (on D3Q19 also Phi_zzz = rho u_z^3, the same defect
+ * of the third moment of f_eq along the third axis).  Its only non-zero
+ * entries are therefore d_a Phi_aaa, one per axis.  The paper does not say how
+ * the derivative is taken; the reading here: at time t, from the pre-collision
+ * rho and half-force u (Eq. macro) of the fluid nodes, by second-order central
+ * differences along axis a, (Phi(x + e_a) - Phi(x - e_a)) / 2, where a
+ * neighbour across a periodic axis wraps; where one neighbour is solid or
+ * beyond a non-periodic edge, the one-sided first-order difference with the
+ * other; where both are, zero. */
+
+/* phi [D][N]: rho u_a^3 at every fluid node, 0 on solid nodes. */
+static void cubic_flux(const or_lattice* L, const or_params* p, const double* f, double* phi) {
+  const size_t N = nnodes(p);
+  for (size_t n = 0; n < N; ++n) {
+    double fl[OR_MAXQ], rho, u[3];
+    if (p->solid && p->solid[n]) {
+      for (int a = 0; a < L->D; ++a) phi[a * N + n] = 0.0;
+      continue;
+    }
+    for (int i = 0; i < L->Q; ++i) fl[i] = f[i * N + n];
+    moments(L, p->force, fl, &rho, u);
+    for (int a = 0; a < L->D; ++a) phi[a * N + n] = rho * u[a] * u[a] * u[a];
+  }
+}
+
+/* dphi [D][N]: d_a Phi_aaa at every fluid node (the reading above), 0 on solids. */
+static void cubic_flux_gradient(const or_lattice* L, const or_params* p, const double* phi,
+                                double* dphi) {
+  const long nx = p->nx, ny = p->ny, nz = p->nz;
+  const long ext[3] = {nx, ny, nz};
+  const size_t N = nnodes(p);
+  for (size_t n = 0; n < N; ++n) {
+    const int solid = p->solid && p->solid[n];
+    const long c[3] = {(long)(n % nx), (long)((n / nx) % ny), (long)(n / (nx * ny))};
+    for (int a = 0; a < L->D; ++a) {
+      if (solid) {
+        dphi[a * N + n] = 0.0;
+        continue;
+      }
+      double v[2];
+      int ok[2];
+      for (int s = 0; s < 2; ++s) {
+        long q[3] = {c[0], c[1], c[2]};
+        q[a] += s ? 1 : -1;
+        ok[s] = 1;
+        if (q[a] < 0 || q[a] >= ext[a]) {
+          if (p->periodic[a])
+            q[a] = (q[a] + ext[a]) % ext[a];
+          else
+            ok[s] = 0;
+        }
+        const size_t m = ok[s] ? (size_t)(q[2] * ny + q[1]) * nx + q[0] : 0;
+        if (ok[s] && p->solid && p->solid[m]) ok[s] = 0;
+        v[s] = ok[s] ? phi[a * N + m] : 0.0;
+      }
+      const double here = phi[a * N + n];
+      double d = 0.0;
+      if (ok[0] && ok[1])
+        d = 0.5 * (v[1] - v[0]);
+      else if (ok[1])
+        d = v[1] - here;
+      else if (ok[0])
+        d = here - v[0];
+      dphi[a * N + n] = d;
+    }
+  }
+}
+
+/* dphi [D][N] = d_a Phi_aaa of the pre-collision state f (for tests). */
+int oracle_cubic_flux_gradient(const or_params* p, const double* f, double* dphi) {
+  or_lattice L;
+  int rc = build_lattice(p->lattice, &L);
+  if (rc) return rc;
+  const size_t N = nnodes(p);
+  double* phi = (double*)malloc(sizeof(double) * L.D * N);
+  if (!phi) return -3;
+  cubic_flux(&L, p, f, phi);
+  cubic_flux_gradient(&L, p, phi, dphi);
+  free(phi);
+  return 0;
+}
+
+/* One node's collision with the Scheme II source, dphi[3][3] = d_g Phi_abg. */
+int oracle_collide_s2(const or_params* p, const double* f, const double* dphi, double* fstar) {
+  or_lattice L;
+  int rc = build_lattice(p->lattice, &L);
+  if (rc) return rc;
+  double t[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) t[a][b] = dphi[3 * a + b];
+  collide_scheme(&L, p, f, fstar, 2, (const double(*)[3])t);
+  return 0;
+}
+
+/* n time steps with the Scheme II source: Phi and its gradient from the
+ * pre-collision state, then collide every fluid node and push-stream as
+ * oracle_step. */
+int oracle_step_s2(const or_params* p, double* f, int nsteps, int nthreads) {
+  or_lattice L;
+  int rc = build_lattice(p->lattice, &L);
+  if (rc) return rc;
+  const int Q = L.Q, D = L.D;
+  const size_t N = nnodes(p);
+  double* fs = (double*)malloc(sizeof(double) * Q * N);
+  double* fn = (double*)malloc(sizeof(double) * Q * N);
+  double* phi = (double*)malloc(sizeof(double) * D * N);
+  double* dphi = (double*)malloc(sizeof(double) * D * N);
+  if (!fs || !fn || !phi || !dphi) {
+    free(fs);
+    free(fn);
+    free(phi);
+    free(dphi);
+    return -3;
+  }
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  for (int s = 0; s < nsteps; ++s) {
+    cubic_flux(&L, p, f, phi);
+    cubic_flux_gradient(&L, p, phi, dphi);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < (long)N; ++n) {
+      double fl[OR_MAXQ], fo[OR_MAXQ], t[3][3] = {{0}};
+      if (p->solid && p->solid[n]) {
+        for (int i = 0; i < Q; ++i) fs[i * N + n] = f[i * N + n];
+        continue;
+      }
+      for (int i = 0; i < Q; ++i) fl[i] = f[i * N + n];
+      for (int a = 0; a < D; ++a) t[a][a] = dphi[a * N + n];
+      collide_scheme(&L, p, fl, fo, 2, (const double(*)[3])t);
+      for (int i = 0; i < Q; ++i) fs[i * N + n] = fo[i];
+    }
+    push_stream(&L, p, f, fs, fn);
+  }
+  free(fs);
+  free(fn);
+  free(phi);
+  free(dphi);
   return 0;
 }
 
