@@ -321,27 +321,41 @@ def copy_ceiling_at(nbytes: int, reps: int = 20) -> dict:
     return out
 
 
+def scheme2_bytes_per_node(lat: str, storage: str) -> int:
+    """Algorithmic bytes of one Scheme II update per node: the rho u_a^3 pass
+    reads Q populations and writes D values, the update reads Q populations and
+    the D values (each once from memory; the neighbours' through L2) and writes
+    Q populations."""
+    D = 2 if lat == "D2Q9" else 3
+    r = 8 if storage == "F64" else 4
+    return 3 * BYTES_PER_NODE[(lat, storage)] // 2 + 2 * D * r
+
+
 def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision="P_TRT",
-              layout: str = "AB"):
+              layout: str = "AB", scheme: int = 1):
     """MLUPS and roofline fraction of another workload (kernel-only, few steps)."""
     import torch
     g = make_lattice(lat, n, storage, collision, layout)
     rho, u = workload_fields(kind, n)
     g.init_equilibrium(rho, u)
+    if scheme == 2:
+        g.set_forcing_scheme(2)
     g.autotune(reps=3, report=False)
     dt = time_kernel(g, 10, 3)
     N = g.N
-    bpn = BYTES_PER_NODE[(lat, storage)]
+    bpn = BYTES_PER_NODE[(lat, storage)] if scheme == 1 else scheme2_bytes_per_node(lat, storage)
     out = {"workload": f"{lat} {collision} {kind} {n}^{2 if lat == 'D2Q9' else 3} {storage}"
-                       + (" AA in place" if layout == "AA" else ""),
+                       + (" AA in place" if layout == "AA" else "")
+                       + (" forcing scheme II (2 launches)" if scheme == 2 else ""),
            "mlups": N / dt / 1e6, "kernel_ms": dt * 1e3,
            "achieved_gbs": bpn * N / dt / 1e9, "frac": bpn * N / dt / 1e9 / peak,
-           "variant": g.variants()[g.variant]}
+           "variant": g.variants()[g.variant] if scheme == 1 else "k_phi + k_step_s2",
+           "bytes_per_node": bpn}
     rc, _ = g.status()
     out["diverged"] = rc != 0
     del g
     torch.cuda.empty_cache()
-    cc = copy_ceiling_at(bpn * N // 2)
+    cc = copy_ceiling_at(BYTES_PER_NODE[(lat, storage)] * N // 2)
     out["copy_ceiling_gbs"] = max(cc["lbm_copy_gbs"], cc["torch_copy_gbs"])
     out["frac_of_copy_ceiling"] = out["achieved_gbs"] / out["copy_ceiling_gbs"]
     return out
@@ -748,6 +762,7 @@ def run_precision_study(args):
 
 def run_case(args):
     """One lattice configuration for a profiler: LATTICE:STORAGE:NX,NY,NZ[:COLLISION[:LAYOUT]],
+    LAYOUT AB, AA or S2 (A/B with forcing scheme II),
     fixed kernel variant (by name; the default variant otherwise), ``--warmup``
     updates then ``--inner`` updates."""
     import torch
@@ -759,6 +774,8 @@ def run_case(args):
     dims = [int(v) for v in parts[2].split(",")]
     coll = parts[3] if len(parts) > 3 else "P_TRT"
     layout = parts[4] if len(parts) > 4 else "AB"
+    scheme = 2 if layout == "S2" else 1
+    layout = "AB" if layout == "S2" else layout
     nx, ny = dims[0], dims[1]
     nz = dims[2] if len(dims) > 2 else 1
     if lat == "D2Q9":
@@ -771,6 +788,8 @@ def run_case(args):
         rho, u = W.channel_at_rest((nz, ny, nx), 3)
         u[0] = 0.02
     g.init_equilibrium(rho, u)
+    if scheme == 2:
+        g.set_forcing_scheme(2)
     if args.variant:
         g.variant = g.variants().index(args.variant)
     g.step(args.warmup)
@@ -893,6 +912,10 @@ def run_ours(args):
             ("d3q19_f64", lambda: secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)),
             ("d3q19_f32_aa",
              lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, layout="AA")),
+            ("d2q9_f32_scheme2",
+             lambda: secondary("D2Q9", n, "F32", "double_shear", peak, scheme=2)),
+            ("d3q19_f32_scheme2",
+             lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, scheme=2)),
             ("batch256", lambda: batched(peak)),
             ("precision", lambda: {"channel": precision_channel((0.1,)),
                                    "taylor_green_3d": precision_flow("taylor_green_3d", 96, 1000),

@@ -195,12 +195,31 @@ int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
  * LBM_ERR_ARG for a periodic x axis, nx < 2 or |u_in| >= 1. */
 int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
 
+/* Body-force scheme of the update (Sec. 2.1): 1 (default) the Guo source of
+ * Eq. source_guo, taken with the single factor (1 - w+/2) so that mass is
+ * conserved for every tau_s2; 2 the simplified projection of Eq. source_simple,
+ * (1 - w+/2) w_i e_i.F / cs^2 plus the cubic-velocity correction G_i of Eq. Gi,
+ * -(1 - w+/2) w_i H2_i,ab d_g Phi_abg / (6 cs^6) with Phi_aaa = rho u_a^3 (the
+ * only non-zero entries; on D3Q19 also Phi_zzz).  G_i is applied with or
+ * without a force.  Its derivative is taken at time t from the pre-collision
+ * rho and half-force u: second-order central differences along each axis, the
+ * one-sided difference where one neighbour is a solid node or beyond a
+ * non-periodic edge, 0 where both are.  Scheme 2 runs two launches per step (a
+ * pass that stores rho u_a^3 of every node in the scratch buffer's field area,
+ * then a one-node-per-thread update; the variant is ignored) and changes
+ * neither the state's layout nor lbm_macros / lbm_diagnostics.
+ * LBM_ERR_ARG for another value; LBM_ERR_UNSUPPORTED for scheme 2 with the AA
+ * layout or with open boundaries on (lbm_set_open_boundaries and
+ * lbm_momentum_exchange also refuse scheme 2); LBM_ERR_STATE on a batch view. */
+int lbm_set_forcing_scheme(lbm_ctx* ctx, int scheme);
+
 /* Force on the solid nodes by momentum exchange (Sec. 3.4), FP64, into out[3]:
  * with halfway bounce-back from resting solids every link from a fluid node to
  * a solid neighbour transfers 2 e_i f*_i, f* the collision of the current state
  * (the force of the next streaming step).  Neighbours beyond a non-periodic
  * edge are walls and not counted.  The drag coefficient of Sec. 3.4 is
- * C_d = 2 out[0] / (rho0 u_c^2 D).  Synchronises. */
+ * C_d = 2 out[0] / (rho0 u_c^2 D).  Synchronises.  LBM_ERR_UNSUPPORTED under
+ * forcing scheme 2. */
 int lbm_momentum_exchange(lbm_ctx* ctx, double out[3]);
 
 /* Synchronises the stream and reports LBM_ERR_DIVERGED if any update since the

@@ -182,6 +182,7 @@ struct lbm_ctx {
   int sms = 0;
   OpenBC open{};  // open boundaries of the square-cylinder benchmark (off by default)
   bool fresh = true;  // the state was written directly (not yet streamed)
+  int scheme = 1;     // forcing scheme: 1 Guo, 2 simplified projection + G_i
   long long wait_ns = 2000000000LL;
   int extra_tx = 0;
 };
@@ -224,6 +225,8 @@ StepLaunch step_of(lbm_ctx* c, const Variant& v) {
   s.parity = (int)(c->t & 1);
   s.v = v;
   s.stream = c->stream;
+  s.scheme = c->scheme;
+  s.phi = c->scratch + c->pl.field_off;
   if (s.layout == LBM_LAYOUT_AA) {
     s.src = c->pop[0];
     s.dst = c->pop[0];
@@ -274,7 +277,7 @@ int ctx_step(lbm_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
     StepLaunch sl = step_of(c, c->vars[c->var]);
     cudaError_t e = c->ops->step(sl);
-    ++c->launches;
+    c->launches += c->scheme == 2 ? 2 : 1;
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "stream-collide launch", e);
     if (c->pl.p.layout == LBM_LAYOUT_AB) c->cur ^= 1;
     ++c->t;
@@ -530,6 +533,7 @@ int lbm_set_open_boundaries(lbm_ctx* c, double u_in, double rho_out) {
     return fail(LBM_ERR_UNSUPPORTED, "open boundaries: D2Q9 with the A/B layout");
   if (c->pl.g.per[0] || c->pl.p.nx < 2)
     return fail(LBM_ERR_ARG, "open boundaries need a non-periodic x axis with nx >= 2");
+  if (c->scheme == 2) return fail(LBM_ERR_UNSUPPORTED, "open boundaries with forcing scheme 2");
   if (!(fabs(u_in) < 1.0)) return fail(LBM_ERR_ARG, "|u_in| must be < 1");
   c->open.on = 1;
   c->open.u_in = u_in;
@@ -537,9 +541,25 @@ int lbm_set_open_boundaries(lbm_ctx* c, double u_in, double rho_out) {
   return LBM_OK;
 }
 
+int lbm_set_forcing_scheme(lbm_ctx* c, int scheme) {
+  CHECK_CTX(c);
+  if (scheme != 1 && scheme != 2) return fail(LBM_ERR_ARG, "forcing scheme must be 1 or 2");
+  if (scheme == 1) {
+    c->scheme = 1;
+    return LBM_OK;
+  }
+  if (c->view) return fail(LBM_ERR_STATE, "batch views take forcing scheme 1 only");
+  if (c->pl.p.layout != LBM_LAYOUT_AB)
+    return fail(LBM_ERR_UNSUPPORTED, "forcing scheme 2: A/B layout only");
+  if (c->open.on) return fail(LBM_ERR_UNSUPPORTED, "forcing scheme 2 with open boundaries");
+  c->scheme = 2;
+  return LBM_OK;
+}
+
 int lbm_momentum_exchange(lbm_ctx* c, double out[3]) {
   CHECK_CTX(c);
   if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+  if (c->scheme == 2) return fail(LBM_ERR_UNSUPPORTED, "momentum exchange with forcing scheme 2");
   double* partials = reinterpret_cast<double*>(c->scratch + kPartialOffset);
   double* res = reinterpret_cast<double*>(c->scratch + kResultOffset);
   int dev_sms = 0;

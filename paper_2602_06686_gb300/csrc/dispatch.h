@@ -54,6 +54,10 @@ struct StepLaunch {
   int layout;     // 0 A/B, 1 AA
   int parity;     // AA: 0 even (local) step, 1 odd (neighbour) step
   Variant v;
+  // forcing: 1 Guo (Eq. source_guo), 2 simplified projection + G_i (Eq. source_simple,
+  // Eq. Gi; two launches, phi = [D][N] values of the arithmetic precision)
+  int scheme;
+  void* phi;
   cudaStream_t stream;
 };
 

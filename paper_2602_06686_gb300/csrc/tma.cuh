@@ -26,6 +26,15 @@
 //
 // Every mbarrier wait is bounded by %globaltimer: on time-out the block sets
 // an error word, lets its issued copies land, and returns.
+//
+// MODE selects what the consumers do with the gathered populations: 0 the
+// update; 1 the first pass of forcing Scheme II (Eq. source_simple, Eq. Gi):
+// store Phi_a = rho u_a^3 of every node, no update; 2 the update followed by
+// the cubic correction G_i from the differences of the stored Phi.  In MODE 2
+// the producer also stages the Phi rows a tile's differences need -- Phi_x of
+// the tile's own row with an x halo, Phi_y of rows y-1, y, y+1 and, on D3Q19,
+// Phi_z of rows z-1, z, z+1, wrapped across periodic axes and skipped beyond
+// walls -- so that they arrive with the populations (TmaPhi).
 #pragma once
 #include <stdint.h>
 
@@ -63,6 +72,8 @@ struct TmaArgs {
   int ntiles;  // ntx * ny * nz (< 2^31)
   long long timeout_ns;
   int extra_tx;  // test hook: extra bytes every stage waits for (never delivered)
+  void* phi;     // MODE 1 / 2: rho u_a^3, [D][nx * ny * nz] (dense node index), precision R
+  R gk;          // MODE 2: -(1 - w+/2) / (6 cs^6)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -221,6 +232,59 @@ __device__ __forceinline__ void tma_source_row(const Geo& G, int i, int y, int z
   }
 }
 
+// Shared-memory rows of the staged Phi in MODE 2 (after the Q population slots
+// of a stage): row 0 Phi_x of the own row over [x0 - HR, x0 + X + HR), rows
+// 1..3 Phi_y and 4..6 Phi_z of the rows at offsets -1, 0, +1, each over
+// [x0, x0 + X) starting at element HR.  HR = 16 bytes of halo.
+template <class L, typename R, int XT>
+struct TmaPhi {
+  static constexpr int kHR = 16 / (int)sizeof(R);
+  static constexpr int kSlot = XT + 2 * kHR;
+  static constexpr int kRows = 1 + 3 * (L::D - 1);
+  static constexpr int kBytes = kRows * kSlot * (int)sizeof(R);
+};
+
+// One-sided / central difference from the neighbour flags and values.
+template <typename R>
+__device__ __forceinline__ R diff3(bool okm, bool okp, R vm, R v0, R vp) {
+  if (okm && okp) return R(0.5) * (vp - vm);
+  if (okp) return vp - v0;
+  if (okm) return v0 - vm;
+  return R(0);
+}
+
+// d_a Phi_a at node (x, y, z), dense index n, for forcing Scheme II: central
+// difference where both neighbours along axis a are fluid nodes (a periodic
+// axis wraps), one-sided where one is solid or beyond a non-periodic edge,
+// zero where both are.
+template <class L, typename R>
+__device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R* __restrict__ phi,
+                                      int d, int x, int y, int z, long long n) {
+  const int c = d == 0 ? x : (d == 1 ? y : z);
+  const int ext = d == 0 ? G.nx : (d == 1 ? G.ny : G.nz);
+  const long long stride = d == 0 ? 1LL : (d == 1 ? (long long)G.nx : (long long)G.nx * G.ny);
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  bool okm = true, okp = true;
+  long long nm = n - stride, np = n + stride;
+  if (c == 0) {
+    if (G.per[d]) nm = n + (long long)(ext - 1) * stride;
+    else okm = false;
+  }
+  if (c == ext - 1) {
+    if (G.per[d]) np = n - (long long)(ext - 1) * stride;
+    else okp = false;
+  }
+  if (mask) {
+    if (okm && mask[nm]) okm = false;
+    if (okp && mask[np]) okp = false;
+  }
+  const R* p = phi + d * N;
+  if (okm && okp) return R(0.5) * (p[np] - p[nm]);
+  if (okp) return p[np] - p[n];
+  if (okm) return p[n] - p[nm];
+  return R(0);
+}
+
 // Resident blocks per SM the register allocation is asked to allow: 4 for
 // 16-bit storage (the collision is then the limiter and more warps hide it), 2
 // for FP32, none for FP64 (whose collision needs the registers).  Measured on
@@ -230,7 +294,7 @@ constexpr int tma_min_blocks() {
   return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
 }
 
-template <class L, int COLL, class S, bool FORCE, bool PACK, int XT>
+template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, int MODE = 0>
 __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
@@ -245,8 +309,10 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + ST;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + ST);
-  T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
-  constexpr long long stage_elems = (long long)L::Q * SLOT;
+  unsigned char* ringb = smem + 128 * ((2 * ST * 8 + 4 + 127) / 128);
+  using Ph = TmaPhi<L, R, XT>;
+  constexpr long long pop_bytes = (long long)L::Q * SLOT * sizeof(T);
+  constexpr long long stage_bytes = pop_bytes + (MODE == 2 ? Ph::kBytes : 0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -295,13 +361,69 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
       if (i < L::Q) tma_source_row_dyn<L>(G, i, y, z, ys, zs, wall);
       const unsigned walls = __ballot_sync(full_mask, i < L::Q && wall);
       const uint32_t fb = smem_addr(full + s);
+      // MODE 2: lane Q + k copies Phi row k of TmaPhi (phr: source row, or -1)
+      long long phr = -1;
+      int phd = 0;
+      uint32_t phbytes = 0;
+      if constexpr (MODE == 2) {
+        const int k = lane - L::Q;
+        if (k >= 0 && k < Ph::kRows) {
+          constexpr uint32_t hrb = (uint32_t)Ph::kHR * sizeof(R);
+          if (k == 0) {
+            phd = 0;
+            phr = (long long)z * G.ny + y;
+            const int plo = max(x0 - Ph::kHR, 0), phi_ = min(xe + Ph::kHR, G.nx);
+            phbytes = (uint32_t)(phi_ - plo) * sizeof(R) + ((lwrap ? hrb : 0u) + (rwrap ? hrb : 0u));
+          } else {
+            phd = (k - 1) / 3 + 1;          // 1: y rows, 2: z rows
+            const int off = (k - 1) % 3 - 1;  // -1, 0, +1
+            int yy = y, zz = z;
+            bool ok = true;
+            if (phd == 1) {
+              yy = y + off;
+              if (yy < 0 || yy >= G.ny) {
+                if (G.per[1]) yy = yy < 0 ? yy + G.ny : yy - G.ny;
+                else ok = false;
+              }
+            } else {
+              zz = z + off;
+              if (zz < 0 || zz >= G.nz) {
+                if (G.per[2]) zz = zz < 0 ? zz + G.nz : zz - G.nz;
+                else ok = false;
+              }
+            }
+            if (ok) {
+              phr = (long long)zz * G.ny + yy;
+              phbytes = (uint32_t)(xe - x0) * sizeof(R);
+            }
+          }
+        }
+        phbytes = __reduce_add_sync(full_mask, phbytes);
+      }
       if (lane == 0) {
         const uint32_t nwrap = (uint32_t)(L::Q - __popc(walls)) * ((lwrap ? 1u : 0u) + (rwrap ? 1u : 0u));
-        mbar_arrive_expect_tx(fb, main_bytes * L::Q + nwrap * halo_bytes + (uint32_t)a.extra_tx);
+        mbar_arrive_expect_tx(fb, main_bytes * L::Q + nwrap * halo_bytes + phbytes + (uint32_t)a.extra_tx);
       }
       __syncwarp();
+      if constexpr (MODE == 2) {
+        if (phr >= 0) {
+          const int k = lane - L::Q;
+          R* prow = reinterpret_cast<R*>(ringb + s * stage_bytes + pop_bytes) + k * Ph::kSlot;
+          const R* gsrc = static_cast<const R*>(a.phi) + (long long)phd * ((long long)G.nx * G.ny * G.nz) +
+                          phr * G.nx;
+          if (k == 0) {
+            constexpr uint32_t hrb = (uint32_t)Ph::kHR * sizeof(R);
+            const int plo = max(x0 - Ph::kHR, 0), phi_ = min(xe + Ph::kHR, G.nx);
+            bulk_g2s(smem_addr(prow + (plo - (x0 - Ph::kHR))), gsrc + plo, (uint32_t)(phi_ - plo) * sizeof(R), fb);
+            if (lwrap) bulk_g2s(smem_addr(prow), gsrc + G.nx - Ph::kHR, hrb, fb);
+            if (rwrap) bulk_g2s(smem_addr(prow + Ph::kHR + (G.nx - x0)), gsrc, hrb, fb);
+          } else {
+            bulk_g2s(smem_addr(prow + Ph::kHR), gsrc + x0, (uint32_t)(xe - x0) * sizeof(R), fb);
+          }
+        }
+      }
       if (i < L::Q) {
-        T* slot = ring + s * stage_elems + i * SLOT;  // slot[k] holds x = x0 - HT + k
+        T* slot = reinterpret_cast<T*>(ringb + s * stage_bytes) + i * SLOT;  // slot[k] holds x = x0 - HT + k
         const int pi = wall ? opp_dyn<L>(i) : i;
         const long long r = wall ? ((long long)z * G.ny + y) : ((long long)zs * G.ny + ys);
         const T* rowp = src + pi * G.plane + r * G.pitch;
@@ -344,7 +466,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
     const int y = w.y, z = w.z;
     const int x0 = w.tx * XT;
     const int wdt = min(XT, G.nx - x0);
-    const T* st = ring + s * stage_elems;
+    const T* st = reinterpret_cast<const T*>(ringb + s * stage_bytes);
     const long long own = ((long long)z * G.ny + y) * G.pitch;
     // tile-uniform: does any plane's source row lie beyond a wall (|e| <= 1, so
     // only boundary rows of a non-periodic axis), or does the tile touch an x
@@ -403,6 +525,27 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
         }
       }
     }
+    R dn[NPT][3];  // MODE 2: d_a Phi_a of this thread's nodes, from the staged rows
+    if constexpr (MODE == 2) {
+      const R* pst = reinterpret_cast<const R*>(reinterpret_cast<const unsigned char*>(st) + pop_bytes);
+      const bool ym = G.per[1] || y > 0, yp = G.per[1] || y < G.ny - 1;
+      const bool zm = G.per[2] || z > 0, zp = G.per[2] || z < G.nz - 1;
+      constexpr int HR = Ph::kHR, SR = Ph::kSlot;
+#pragma unroll
+      for (int n = 0; n < NPT; ++n) {
+        const int j = jn[n];
+        const int x = x0 + j;
+        const R* px = pst + HR + j;
+        const R* py = pst + SR + HR + j;
+        dn[n][0] = act[n] ? diff3<R>(G.per[0] || x > 0, G.per[0] || x < G.nx - 1, px[-1], px[0], px[1]) : R(0);
+        dn[n][1] = act[n] ? diff3<R>(ym, yp, py[0], py[SR], py[2 * SR]) : R(0);
+        dn[n][2] = R(0);
+        if constexpr (L::D == 3) {
+          const R* pz = pst + 4 * SR + HR + j;
+          dn[n][2] = act[n] ? diff3<R>(zm, zp, pz[0], pz[SR], pz[2 * SR]) : R(0);
+        }
+      }
+    }
     // the stage is no longer read: release it before computing
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_addr(empty + s));
@@ -410,7 +553,62 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S
       s = 0;
       ++u;
     }
+    const long long rowd = ((long long)z * G.ny + y) * G.nx + x0;  // dense index of x0
+    const long long Nd = (long long)G.nx * G.ny * G.nz;
+    if constexpr (MODE == 1) {
+      // rho and the half-force u (Eq. macro), then Phi_a = rho u_a^3
+      using A = Ar<V>;
+      V drho = g[0];
+      V j[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) j[d] = A::c(0.0);
+#pragma unroll
+      for (int i = 1; i < L::Q; ++i) {
+        drho = A::add(drho, g[i]);
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+          const int e = d == 0 ? L::cx(i) : (d == 1 ? L::cy(i) : L::cz(i));
+          if (e == 1) j[d] = A::add(j[d], g[i]);
+          if (e == -1) j[d] = A::sub(j[d], g[i]);
+        }
+      }
+      const V rho = A::add(A::c(a.c.rho0), drho);
+      const V inv = A::rcp(rho);
+      R* ph = static_cast<R*>(a.phi);
+#pragma unroll
+      for (int d = 0; d < L::D; ++d) {
+        const V ud = FORCE ? A::mul(A::add(j[d], A::c(a.c.Fh[d])), inv) : A::mul(j[d], inv);
+        const V p = A::mul(A::mul(rho, ud), A::mul(ud, ud));
+        R* pd = ph + d * Nd + rowd;
+        if constexpr (PACK) {
+          if (act[0]) pd[jn[0]] = p.x;
+          if (act[NPT - 1]) pd[jn[NPT - 1]] = p.y;
+        } else {
+          if (act[0]) pd[jn[0]] = p;
+        }
+      }
+      continue;
+    }
     const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
+    if constexpr (MODE == 2) {
+      // G_i = gk w_i (sum_a e_ia^2 D_a - (1/3) sum_a D_a), D_a = d_a Phi_a
+      using A = Ar<V>;
+      V dv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if constexpr (PACK) dv[d] = F2{dn[0][d], dn[NPT - 1][d]};
+        else dv[d] = dn[0][d];
+      }
+      const V third = A::mul(A::add(A::add(dv[0], dv[1]), dv[2]), A::c(1.0 / 3.0));
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        V h = A::sub(A::c(0.0), third);
+        if (L::cx(i)) h = A::add(h, dv[0]);
+        if (L::cy(i)) h = A::add(h, dv[1]);
+        if (L::cz(i)) h = A::add(h, dv[2]);
+        g[i] = A::fma(A::c(R(a.gk * R(L::w(i)))), h, g[i]);
+      }
+    }
     bool anybad = act[0] && (bad & 1u);
     if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
     T* op = dst + own + x0;

@@ -129,6 +129,80 @@ __global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R>
   record_bad(a.flag, a.step, bad);
 }
 
+// ---- Scheme II forcing (Eq. source_simple, Eq. Gi), two launches per step.
+// The cubic correction G_i needs d_g Phi_abg of the pre-collision state, whose
+// only non-zero entries are d_a (rho u_a^3); a node's derivative needs its
+// neighbours' rho and u at the same time level, which the fused pull kernel of
+// one node does not have.  So k_phi first stores Phi_a = rho u_a^3 of every
+// fluid node ([D][N], arithmetic precision R), then k_step_s2 gathers, takes
+// the differences, collides with the F_i projection in place of the Guo
+// source and adds G_i.  Differences along axis a: central where both
+// neighbours are fluid nodes (a periodic axis wraps), one-sided where one is
+// solid or beyond a non-periodic edge, zero where both are.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_phi(const StepArgs<typename S::R> a, typename S::R* phi) {
+  using R = typename S::R;
+  using T = typename S::T;
+  const Geo& G = a.g;
+  const RowNode q(G);
+  if (!q.valid || (a.mask && a.mask[q.n])) return;
+  const T* __restrict__ src = static_cast<const T*>(a.src);
+  R drho = R(0), j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const R v = S::dec(src[ab_slot<L>(G, a.mask, q.x, q.y, q.z, i)]);
+    drho += v;
+    if (L::cx(i)) j[0] += R(L::cx(i)) * v;
+    if (L::cy(i)) j[1] += R(L::cy(i)) * v;
+    if (L::cz(i)) j[2] += R(L::cz(i)) * v;
+  }
+  const R rho = a.c.rho0 + drho;
+  const R inv = R(1) / rho;
+  const long long N = (long long)G.nx * G.ny * G.nz;
+#pragma unroll
+  for (int d = 0; d < L::D; ++d) {
+    const R u = (j[d] + a.c.Fh[d]) * inv;
+    phi[d * N + q.n] = rho * u * u * u;
+  }
+}
+
+// The step with the Scheme II source.  a.c carries no symmetric Guo terms
+// (fe = fu = 0), so collide_v leaves f_eq + (1 - w+) R2 + (1 - w-) R3 plus the
+// antisymmetric force content F_i/2 + (1 - w-) F_i/2, which is what
+// (1 - w+) R1 + (1 - w+/2) F_i + (1 - w-) F_i/2 amounts to; then
+//   G_i = gk w_i (sum_a e_ia^2 D_a - (1/3) sum_a D_a),  gk = -(1 - w+/2) / (6 cs^6) = -4.5 (1 - w+/2),
+// i.e. -(1 - w+/2) w_i H2_i:dPhi / (6 cs^6) for the diagonal dPhi = diag(D_a).
+template <class L, int COLL, bool FORCE, class S>
+__global__ void __launch_bounds__(256) k_step_s2(const StepArgs<typename S::R> a,
+                                                 const typename S::R* __restrict__ phi,
+                                                 typename S::R gk) {
+  using R = typename S::R;
+  using T = typename S::T;
+  const Geo& G = a.g;
+  const RowNode q(G);
+  if (!q.valid || (a.mask && a.mask[q.n])) return;
+  const T* __restrict__ src = static_cast<const T*>(a.src);
+  T* __restrict__ dst = static_cast<T*>(a.dst);
+  R g[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) g[i] = S::dec(src[ab_slot<L>(G, a.mask, q.x, q.y, q.z, i)]);
+  R Dg[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int d = 0; d < L::D; ++d) Dg[d] = phi_grad<L, R>(G, a.mask, phi, d, q.x, q.y, q.z, q.n);
+  const bool bad = collide_v<L, COLL, FORCE, R>(g, a.c) != 0u;
+  const R third = (Dg[0] + Dg[1] + Dg[2]) * R(1.0 / 3.0);
+  const long long own = ((long long)q.z * G.ny + q.y) * G.pitch + q.x;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    R h = -third;
+    if (L::cx(i)) h += Dg[0];
+    if (L::cy(i)) h += Dg[1];
+    if (L::cz(i)) h += Dg[2];
+    dst[i * G.plane + own] = S::enc(g[i] + gk * R(L::w(i)) * h);
+  }
+  record_bad(a.flag, a.step, bad);
+}
+
 template <class L, class S>
 __global__ void __launch_bounds__(256) k_init_eq(Geo G, const uint8_t* mask, int layout, int parity,
                                                  typename S::T* pop, const double* rho,
@@ -527,7 +601,7 @@ struct TU {
     return head + (size_t)stages * L::Q * (size_t)(X + 2 * H) * sizeof(T);
   }
 
-  template <int COLL, bool FORCE, int XT>
+  template <int COLL, bool FORCE, int XT, int MODE = 0>
   static cudaError_t go_tma_x(const StepLaunch& s) {
     using Sh = TmaShape<XT, kPack>;
     TmaArgs<R> a;
@@ -545,13 +619,27 @@ struct TU {
     a.ntiles = (int)ntiles;
     a.timeout_ns = s.wait_ns > 0 ? s.wait_ns : 2000000000LL;
     a.extra_tx = s.extra_tx;
-    const size_t smem = tma_smem(XT, a.stages);
+    a.phi = s.phi;
+    a.gk = R(0);
+    if (MODE == 2) {
+      CoefV<double> c = s.c;  // the F_i projection: no symmetric Guo terms
+      for (int i = 0; i < kQMax; ++i) c.fe[i] = c.fu[i] = 0.0;
+      a.c = coef_cast<R>(c);
+      a.gk = R(-4.5 * (1.0 - 0.5 * (1.0 - s.c.cp)));
+    }
+    size_t smem = tma_smem(XT, a.stages);
+    if (MODE == 2 && smem > 0) smem += (size_t)a.stages * TmaPhi<L, R, XT>::kBytes;
     if (smem == 0 || smem > 227 * 1024 || a.stages > 8) return cudaErrorInvalidValue;
-    // 0: A/B, 1: AA even step, 2: AA odd step
-    const int kind = s.layout == 1 ? 1 + (s.parity & 1) : 0;
-    void (*kern)(TmaArgs<R>) = kind == 0   ? &k_step_tma<L, COLL, S, FORCE, kPack, XT>
-                               : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
-                                           : &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>;
+    // 0: A/B, 1: AA even step, 2: AA odd step (MODE 0); MODE 1 / 2: A/B only
+    const int kind = MODE != 0 ? 0 : (s.layout == 1 ? 1 + (s.parity & 1) : 0);
+    void (*kern)(TmaArgs<R>);
+    if constexpr (MODE != 0) {
+      kern = &k_step_tma<L, COLL, S, FORCE, kPack, XT, MODE>;
+    } else {
+      kern = kind == 0   ? &k_step_tma<L, COLL, S, FORCE, kPack, XT>
+             : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
+                         : &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>;
+    }
     // per instantiation and kind: the shared-memory opt-in (once) and the
     // resident blocks per SM for each ring depth (cached)
     static bool attr_set[3] = {false, false, false};
@@ -676,7 +764,83 @@ struct TU {
     return reduce_partials(partials, blocks, out, a.stream);
   }
 
+  // Scheme II on the pipelined kernel (no solid mask, rows of whole 16-byte
+  // units): the tile width and ring depth of the chosen pipelined variant, the
+  // update's ring reduced until it holds the staged Phi rows within 200 KB;
+  // under a register variant the widest tile with a two-deep ring (four for FP64).
+  template <int COLL, bool FORCE, int XT>
+  static cudaError_t go_s2_tma_x(const StepLaunch& s, int st) {
+    StepLaunch t = s;
+    t.v = Variant{1, 0, 0, 0, XT, st};
+    cudaError_t e = go_tma_x<C_TRT, FORCE, XT, 1>(t);
+    if (e != cudaSuccess) return e;
+    while (st > 2 && tma_smem(XT, st) + (size_t)st * TmaPhi<L, R, XT>::kBytes > 200 * 1024) --st;
+    t.v.stages = st;
+    return go_tma_x<COLL, FORCE, XT, 2>(t);
+  }
+  template <int COLL, bool FORCE>
+  static cudaError_t go_s2_tma(const StepLaunch& s) {
+    const int X = s.v.kind == 1 ? s.v.X : (kPack ? 512 : 128);
+    const int st = s.v.kind == 1 ? s.v.stages : (kPack ? 2 : 4);
+    if constexpr (kPack) {
+      switch (X) {
+        case 256:
+          return go_s2_tma_x<COLL, FORCE, 256>(s, st);
+        case 384:
+          return go_s2_tma_x<COLL, FORCE, 384>(s, st);
+        case 512:
+          return go_s2_tma_x<COLL, FORCE, 512>(s, st);
+      }
+    } else {
+      switch (X) {
+        case 128:
+          return go_s2_tma_x<COLL, FORCE, 128>(s, st);
+        case 192:
+          return go_s2_tma_x<COLL, FORCE, 192>(s, st);
+        case 256:
+          return go_s2_tma_x<COLL, FORCE, 256>(s, st);
+      }
+    }
+    return cudaErrorInvalidValue;
+  }
+  static bool s2_tma_ok(const StepLaunch& s) {
+    constexpr int H = 16 / (int)sizeof(T);
+    return s.mask == nullptr && s.g.nx % H == 0 && s.g.nx >= 2 * H;
+  }
+
+  template <int COLL, bool FORCE>
+  static cudaError_t go_s2(const StepLaunch& s) {
+    if (s2_tma_ok(s)) return go_s2_tma<COLL, FORCE>(s);
+    const dim3 grid((unsigned)((long long)s.g.ny * s.g.nz), (unsigned)((s.g.nx + 255) / 256));
+    R* phi = static_cast<R*>(s.phi);
+    StepArgs<R> a = args(s);
+    k_phi<L, S><<<grid, 256, 0, s.stream>>>(a, phi);
+    CoefV<double> c = s.c;  // the F_i projection: no symmetric Guo terms
+    for (int i = 0; i < kQMax; ++i) c.fe[i] = c.fu[i] = 0.0;
+    a.c = coef_cast<R>(c);
+    const R gk = R(-4.5 * (1.0 - 0.5 * (1.0 - s.c.cp)));
+    k_step_s2<L, COLL, FORCE, S><<<grid, 256, 0, s.stream>>>(a, phi, gk);
+    return cudaGetLastError();
+  }
+  template <int COLL>
+  static cudaError_t s2_coll(const StepLaunch& s) {
+    return s.force ? go_s2<COLL, true>(s) : go_s2<COLL, false>(s);
+  }
+  static cudaError_t step_s2(const StepLaunch& s) {
+    if (s.layout != 0 || s.phi == nullptr || s.open.on) return cudaErrorInvalidValue;
+    switch (s.collision) {
+      case C_TRT:
+        return s2_coll<C_TRT>(s);
+      case C_TRT_RLB:
+        return s2_coll<C_TRT_RLB>(s);
+      case C_P_TRT:
+        return s2_coll<C_P_TRT>(s);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t step(const StepLaunch& s) {
+    if (s.scheme == 2) return step_s2(s);
     if (s.open.on) return step_open(s);
     if (s.v.kind == 1) return step_tma(s);
     switch (s.v.nv) {

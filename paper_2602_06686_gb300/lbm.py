@@ -36,7 +36,7 @@ EXPORTED = [
     "lbm_batch_step", "lbm_batch_variant_count", "lbm_batch_variant_name",
     "lbm_batch_set_variant", "lbm_batch_autotune", "lbm_batch_set_barrier",
     "lbm_batch_launches", "lbm_batch_destroy", "lbm_diagnostics_noalloc",
-    "lbm_set_open_boundaries", "lbm_momentum_exchange",
+    "lbm_set_open_boundaries", "lbm_momentum_exchange", "lbm_set_forcing_scheme",
 ]
 
 
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_diagnostics_noalloc": ([pp, vp, vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
         "lbm_set_open_boundaries": ([vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
         "lbm_momentum_exchange": ([vp, dp], ctypes.c_int),
+        "lbm_set_forcing_scheme": ([vp, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -283,6 +284,11 @@ class Lattice:
         right (D2Q9, A/B, x non-periodic); rho_out <= 0 turns them off."""
         _check(self.lib.lbm_set_open_boundaries(self.ctx, float(u_in), float(rho_out)),
                "lbm_set_open_boundaries")
+
+    def set_forcing_scheme(self, scheme: int):
+        """1: Guo source (default); 2: the simplified projection with the cubic
+        correction G_i (Eq. source_simple, Eq. Gi), two launches per step."""
+        _check(self.lib.lbm_set_forcing_scheme(self.ctx, int(scheme)), "lbm_set_forcing_scheme")
 
     def momentum_exchange(self) -> np.ndarray:
         """Force on the solid nodes by momentum exchange, FP64 (3 components)."""
