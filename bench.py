@@ -349,7 +349,7 @@ def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision=
                        + (" forcing scheme II (2 launches)" if scheme == 2 else ""),
            "mlups": N / dt / 1e6, "kernel_ms": dt * 1e3,
            "achieved_gbs": bpn * N / dt / 1e9, "frac": bpn * N / dt / 1e9 / peak,
-           "variant": g.variants()[g.variant] if scheme == 1 else "k_phi + k_step_s2",
+           "variant": g.variants()[g.variant],
            "bytes_per_node": bpn}
     rc, _ = g.status()
     out["diverged"] = rc != 0

@@ -204,10 +204,14 @@ int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
  * without a force.  Its derivative is taken at time t from the pre-collision
  * rho and half-force u: second-order central differences along each axis, the
  * one-sided difference where one neighbour is a solid node or beyond a
- * non-periodic edge, 0 where both are.  Scheme 2 runs two launches per step (a
+ * non-periodic edge, 0 where both are.  Scheme 2 runs two launches per step: a
  * pass that stores rho u_a^3 of every node in the scratch buffer's field area,
- * then a one-node-per-thread update; the variant is ignored) and changes
- * neither the state's layout nor lbm_macros / lbm_diagnostics.
+ * then the update.  Without a solid mask and with rows of whole 16-byte units
+ * both run on the pipelined kernel (the update copies the rho u^3 rows a tile
+ * needs through its ring) with the tile width and ring depth of the selected
+ * pipelined variant, or the widest tile under a register variant; otherwise
+ * on one-node-per-thread kernels.  It changes neither the state's layout nor
+ * lbm_macros / lbm_diagnostics.
  * LBM_ERR_ARG for another value; LBM_ERR_UNSUPPORTED for scheme 2 with the AA
  * layout or with open boundaries on (lbm_set_open_boundaries and
  * lbm_momentum_exchange also refuse scheme 2); LBM_ERR_STATE on a batch view. */
@@ -291,8 +295,9 @@ int lbm_set_variant(lbm_ctx* ctx, int v);
  * which the next step overwrites).  AA layout: there is no spare buffer, so the
  * trials are real steps in pairs (even, odd): the lattice advances by
  * 2 (reps + 1) steps per variant and the step counter with it.  Results are
- * cached per (lattice, storage, collision, mask, extent, layout) for the
- * process; a cached answer (times_ms NULL) runs nothing.  Synchronises. */
+ * cached per (lattice, storage, collision, mask, extent, layout, forcing
+ * scheme) for the process; a cached answer (times_ms NULL) runs nothing.
+ * Under forcing scheme 2 the trials are scheme-2 steps.  Synchronises. */
 int lbm_autotune(lbm_ctx* ctx, int reps, int* chosen, float* times_ms);
 
 int lbm_destroy(lbm_ctx* ctx);

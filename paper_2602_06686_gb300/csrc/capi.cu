@@ -673,12 +673,12 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   CHECK_CTX(c);
   if (reps < 1) reps = 1;
   const bool aa = c->pl.p.layout == LBM_LAYOUT_AA;
-  using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
+  using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int>;
   static std::mutex mu;
   static std::map<Key, int> cache;
   const Key key{c->pl.p.lattice, c->pl.p.storage, c->pl.kernel_collision, c->mask != nullptr,
                 c->pl.p.nx,      c->pl.p.ny,      c->pl.p.nz,            c->pl.g.per[0],
-                c->pl.g.per[1],  c->pl.g.per[2],        c->pl.p.layout};
+                c->pl.g.per[1],  c->pl.g.per[2],  c->pl.p.layout,        c->scheme};
   if (!times_ms) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -704,7 +704,7 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
     if (!aa) {
       StepLaunch sl = step_of(c, c->vars[v]);  // reads the state, writes the other buffer
       e = c->ops->step(sl);
-      c->launches += 1 + reps;
+      c->launches += (1 + reps) * (c->scheme == 2 ? 2 : 1);
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r) e = c->ops->step(sl);
     } else {
