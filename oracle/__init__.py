@@ -29,11 +29,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
 TRT, TRT_RLB, P_TRT, BGK, RLB = 0, 1, 2, 3, 4
 COLLISIONS = {"TRT": TRT, "TRT_RLB": TRT_RLB, "P_TRT": P_TRT, "BGK": BGK, "RLB": RLB}
-Q_OF = {D2Q9: 9, D3Q19: 19}
-D_OF = {D2Q9: 2, D3Q19: 3}
+Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
+D_OF = {D2Q9: 2, D3Q19: 3, D3Q27: 3}
 
 
 def build(force: bool = False) -> str:
@@ -81,6 +81,7 @@ def _load():
         lib.oracle_cubic_flux_gradient.argtypes = [pp, dp, dp]
         lib.oracle_collide_s2.argtypes = [pp, dp, dp, dp]
         lib.oracle_step_s2.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_fifth_order_projection.argtypes = [ctypes.c_int, dp, dp]
         _lib = lib
     return _lib
 
@@ -155,8 +156,8 @@ def lattice_info(lattice: int) -> dict:
     e = np.zeros((Q, 3), dtype=np.int32)
     w = np.zeros(Q)
     opp = np.zeros(Q, dtype=np.int32)
-    phi = np.zeros((3, Q))
-    nrm = np.zeros(3)
+    phi = np.zeros((7, Q))
+    nrm = np.zeros(7)
     rc = lib.oracle_lattice_info(lattice, ctypes.byref(D), ctypes.byref(Qo), ctypes.byref(NG),
                                  e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
                                  opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(phi),
@@ -186,6 +187,17 @@ def hermite_contraction(lattice: int, g: np.ndarray):
     if lib.oracle_hermite_contraction(lattice, _dp(g), _dp(r2), _dp(r3)):
         raise RuntimeError("oracle_hermite_contraction failed")
     return r2, r3
+
+
+def fifth_order_projection(lattice: int, g: np.ndarray) -> np.ndarray:
+    """P^(5) g on D3Q27: projection onto the fifth-order antisymmetric modes of
+    App. D3Q27 (the residual the hybrid P-TRT keeps in R3)."""
+    lib = _load()
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros_like(g)
+    if lib.oracle_fifth_order_projection(lattice, _dp(g), _dp(out)):
+        raise RuntimeError("oracle_fifth_order_projection failed")
+    return out
 
 
 def hermite_ranks(lattice: int):

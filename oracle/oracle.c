@@ -65,11 +65,11 @@
 #include <omp.h>
 #endif
 
-#define OR_MAXQ 19
-#define OR_MAXG 3
+#define OR_MAXQ 27
+#define OR_MAXG 7
 #define OR_CS2 (1.0 / 3.0)
 
-enum { OR_D2Q9 = 0, OR_D3Q19 = 1 };
+enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
 enum { OR_TRT = 0, OR_TRT_RLB = 1, OR_P_TRT = 2, OR_BGK = 3, OR_RLB = 4 };
 
 typedef struct {
@@ -140,6 +140,26 @@ static int build_lattice(int which, or_lattice* L) {
       }
       L->w[i] = (n2 == 0) ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
     }
+  } else if (which == OR_D3Q27) {
+    /* App. D3Q27: rest; +-x, +-y, +-z; the 12 face diagonals as for D3Q19; the
+     * 8 body diagonals in inversion pairs (+++, ---), (++-, --+), (+-+, -+-),
+     * (-++, +--).  Weights: products of the D1Q3 weights 2/3 (0) and 1/6 (+-1),
+     * i.e. 8/27, 2/27, 1/54, 1/216 (not printed; the tensor-product lattice). */
+    static const int v[27][3] = {
+        {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+        {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+        {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},  {1, 1, 1},   {-1, -1, -1},
+        {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+    L->D = 3;
+    L->Q = 27;
+    for (int i = 0; i < 27; ++i) {
+      double w = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        L->e[i][a] = v[i][a];
+        w *= v[i][a] == 0 ? 2.0 / 3.0 : 1.0 / 6.0;
+      }
+      L->w[i] = w;
+    }
   } else {
     return -1;
   }
@@ -184,13 +204,29 @@ static int build_lattice(int which, or_lattice* L) {
       for (int i = 0; i < L->Q; ++i) hyd[k][i] -= c * hyd[m][i];
     }
   }
+  /* Candidates: the fourth-order products for a < b; on D3Q27 also the
+   * sixth-order product and the three shear-energy modes of App. D3Q27
+   * (G4 = (ex2-cs2)(ey2-cs2)(ez2-cs2)/cs2, G5..G7 = e_a e_b (e_c^2 - cs2)). */
+  const int ncand = (D * (D - 1)) / 2 + (L->Q == 27 ? 4 : 0);
   int ng = 0;
-  for (int a = 0; a < D; ++a)
-    for (int b = a + 1; b < D; ++b) {
+  for (int k = 0; k < ncand; ++k) {
       double cand[OR_MAXQ];
-      for (int i = 0; i < L->Q; ++i)
-        cand[i] = ((double)L->e[i][a] * L->e[i][a] - OR_CS2) *
-                  ((double)L->e[i][b] * L->e[i][b] - OR_CS2);
+      for (int i = 0; i < L->Q; ++i) {
+        const double q[3] = {(double)L->e[i][0] * L->e[i][0] - OR_CS2,
+                             (double)L->e[i][1] * L->e[i][1] - OR_CS2,
+                             (double)L->e[i][2] * L->e[i][2] - OR_CS2};
+        if (k < (D * (D - 1)) / 2) {
+          const int a = (k < D - 1) ? 0 : 1, b = (k < D - 1) ? k + 1 : 2;
+          cand[i] = q[a] * q[b];
+        } else if (k == 3) {
+          cand[i] = q[0] * q[1] * q[2] / OR_CS2;
+        } else {
+          const int c = k - 4; /* G5: xy(z), G6: yz(x), G7: zx(y) */
+          const int a = c == 0 ? 0 : (c == 1 ? 1 : 2), b = c == 0 ? 1 : (c == 1 ? 2 : 0);
+          const int cc = 3 - a - b;
+          cand[i] = (double)L->e[i][a] * L->e[i][b] * q[cc];
+        }
+      }
       for (int m = 0; m < nh; ++m) {
         double c = dot_w(L, cand, hyd[m]) / dot_w(L, hyd[m], hyd[m]);
         for (int i = 0; i < L->Q; ++i) cand[i] -= c * hyd[m][i];
@@ -204,7 +240,7 @@ static int build_lattice(int which, or_lattice* L) {
       for (int i = 0; i < L->Q; ++i) L->phi[ng][i] = cand[i];
       L->phinorm[ng] = nrm;
       ++ng;
-    }
+  }
   L->NG = ng;
   /* Orthogonal bases of the Hermite spans used by the "Hermite projections" of
    * Eq. R2R3_hermite, read as w-orthogonal projections onto span{H2_ab} and
@@ -358,7 +394,14 @@ static void collide_scheme(const or_lattice* L, const or_params* p, const double
         R3 = fm[i] + 0.5 * Fi;
         break;
       case OR_P_TRT:
-        R2 = fp[i] - pg[i];
+        if (Q == 27) {
+          /* Eq. PTRT_D3Q27, the hybrid: N_G = 7 > M_2 = 6, so the second-order
+           * term is the tensor (Hermite) projection, the third-order term the
+           * antisymmetric approximation (fifth-order residual kept). */
+          R2 = R2h[i];
+        } else {
+          R2 = fp[i] - pg[i];
+        }
         R3 = fm[i] + 0.5 * Fi;
         break;
       case OR_TRT_RLB:
@@ -964,6 +1007,26 @@ double oracle_l2(long n, const double* qn, const double* qa) {
     den += qa[k] * qa[k];
   }
   return sqrt(num / den);
+}
+
+/* P^(5) g on D3Q27 (App. D3Q27): the w-orthogonal projection onto the three
+ * fifth-order antisymmetric modes psi^(5,x) = e_x (e_y^2 - cs2)(e_z^2 - cs2) and
+ * its cyclic permutations, the part of fneq- outside span{H1, H3}.  For tests. */
+int oracle_fifth_order_projection(int lattice, const double* g, double* out) {
+  or_lattice L;
+  int rc = build_lattice(lattice, &L);
+  if (rc) return rc;
+  if (L.Q != 27) return -4;
+  double psi[3][OR_MAXQ], nrm[3];
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    for (int i = 0; i < L.Q; ++i)
+      psi[a][i] = L.e[i][a] * ((double)L.e[i][b] * L.e[i][b] - OR_CS2) *
+                  ((double)L.e[i][c] * L.e[i][c] - OR_CS2);
+    nrm[a] = dot_w(&L, psi[a], psi[a]);
+  }
+  project(&L, 3, (const double(*)[OR_MAXQ])psi, nrm, g, out);
+  return 0;
 }
 
 /* The literal Hermite contractions of Eq. R2R3_hermite, for tests only:

@@ -1,0 +1,215 @@
+"""Pins of the oracle on D3Q27 (App. D3Q27, Eq. PTRT_D3Q27, Rmk D3Q27): the
+lattice tables, the printed subspace structure (Tab. lattice_summary,
+sym_structure, antisym_structure), the printed ghost and fifth-order modes,
+and the hybrid P-TRT against Thm 2nd and against TRT-RLB up to exactly the
+fifth-order residual the appendix names.
+
+Each check is fixed by something other than the oracle's own formulas: the
+printed tables and modes, the isotropy of the tensor-product lattice, a
+theorem relating two different formulas, or a brute-force rank."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+CS2 = 1.0 / 3.0
+LAT = O.D3Q27
+
+
+def _info():
+    return O.lattice_info(LAT)
+
+
+def _printed_ghosts(e):
+    """G1..G7 as printed in App. D3Q27."""
+    q = e.astype(float) ** 2 - CS2
+    x, y, z = (e[:, a].astype(float) for a in range(3))
+    return np.array([q[:, 0] * q[:, 1], q[:, 1] * q[:, 2], q[:, 2] * q[:, 0],
+                     q[:, 0] * q[:, 1] * q[:, 2] / CS2,
+                     x * y * q[:, 2], y * z * q[:, 0], z * x * q[:, 1]])
+
+
+def _printed_fifth(e):
+    """psi^(5,x) = e_x (e_y^2 - cs^2)(e_z^2 - cs^2) and its cyclic permutations."""
+    q = e.astype(float) ** 2 - CS2
+    return np.array([e[:, a] * q[:, (a + 1) % 3] * q[:, (a + 2) % 3] for a in range(3)])
+
+
+def _wproj(w, modes, g):
+    """w-orthogonal projection of a population vector g onto span{modes}
+    (modes mutually w-orthogonal): w_i sum_k m_k,i <m_k, g> / <m_k, m_k>_w."""
+    out = np.zeros_like(g)
+    for m in modes:
+        out += w * m * (m @ g) / np.sum(w * m * m)
+    return out
+
+
+def test_tables_are_the_tensor_product_lattice():
+    """27 velocities (1 rest, 6 axial, 12 face, 8 body diagonals), weights the
+    products of the D1Q3 weights, isotropic to sixth order with cs^2 = 1/3."""
+    info = _info()
+    e, w = info["e"].astype(float), info["w"]
+    assert {tuple(v) for v in info["e"]} == set(itertools.product((-1, 0, 1), repeat=3))
+    n2 = (e ** 2).sum(1)
+    assert [int(np.sum(n2 == k)) for k in range(4)] == [1, 6, 12, 8]
+    np.testing.assert_allclose(w, np.prod(np.where(e == 0, 2 / 3, 1 / 6), axis=1), rtol=1e-15)
+    assert np.all(e[info["opp"]] == -e)
+    I = np.eye(3)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, e, e), CS2 * I, atol=1e-15)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)
+    want4 = CS2 ** 2 * (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+                        + np.einsum("ad,bc->abcd", I, I))
+    np.testing.assert_allclose(m4, want4, atol=1e-15)
+    assert np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2 * e[:, 2] ** 2) == pytest.approx(CS2 ** 3)
+
+
+def test_subspace_structure_matches_printed_tables(golden):
+    """Tab. lattice_summary / sym_structure / antisym_structure, D3Q27 row:
+    dim S = 14, dim A = 13, N_G = 7, M2 = 6, N3 = 7, and D + N3 = 10 < dim A
+    (the deficit of 3 the paper attributes to fifth-order modes)."""
+    row = [r for r in golden("lattice_summary.txt") if r[0] == "D3Q27"][0]
+    Q, D, Q0, Qp, dS, dA, NG, N3, M2 = map(int, row[1:])
+    info = _info()
+    assert info["Q"] == Q and info["D"] == D and info["NG"] == NG
+    assert Q0 + Qp == dS and Qp == dA
+    n2, n3 = O.hermite_ranks(LAT)
+    assert (n2, n3) == (M2, N3)
+    assert D + n3 == 10 and dA - (D + n3) == 3
+    e = info["e"].astype(float)
+    H2, H3 = O.hermite(LAT)
+    h3 = np.array([H3[:, a, b, c] for a in range(3) for b in range(a, 3) for c in range(b, 3)])
+    anti = np.vstack([e.T, h3, _printed_fifth(info["e"])])
+    assert np.linalg.matrix_rank(anti, tol=1e-12) == dA  # H1 + H3 + psi5 span A
+
+
+def test_printed_ghost_modes_complete_the_symmetric_subspace():
+    """App. D3Q27 calls G1..G7 orthogonal ghost modes: they are mutually
+    w-orthogonal, w-orthogonal to 1 and to every H2 component, and with them
+    span the 14-dimensional symmetric subspace; the oracle's ghost basis spans
+    the same space."""
+    info = _info()
+    e, w = info["e"], info["w"]
+    G = _printed_ghosts(e)
+    gram = (G * w) @ G.T
+    np.testing.assert_allclose(gram - np.diag(np.diag(gram)), 0.0, atol=1e-16)
+    H2, _ = O.hermite(LAT)
+    hyd = np.vstack([np.ones(27)] + [H2[:, a, b] for a in range(3) for b in range(a, 3)])
+    np.testing.assert_allclose((hyd * w) @ G.T, 0.0, atol=1e-16)
+    assert np.linalg.matrix_rank(np.vstack([hyd, G]), tol=1e-12) == 14
+    assert np.linalg.matrix_rank(np.vstack([G, info["phi"]]), tol=1e-12) == 7
+
+
+def _state(rng, F=(0.0, 0.0, 0.0)):
+    u = 0.08 * rng.standard_normal(3)
+    f = O.equilibrium(LAT, 1.0 + 0.02 * rng.standard_normal(), u)
+    return f * (1.0 + 0.02 * rng.standard_normal(27))
+
+
+def _fneq(info, f, F=(0.0, 0.0, 0.0)):
+    e = info["e"].astype(float)
+    rho = f.sum()
+    u = (e.T @ f + 0.5 * np.asarray(F)) / rho
+    return f - O.equilibrium(LAT, rho, u)
+
+
+def test_hybrid_second_order_term_is_the_ghost_purified_one():
+    """Thm 2nd on D3Q27: the hybrid's tensor projection R2 equals
+    fneq+ - P_G fneq with P_G built from the printed G1..G7.  R2 is read off
+    the oracle collision at w- = 1 (no antisymmetric relaxation) and F = 0."""
+    info = _info()
+    w, opp = info["w"], info["opp"]
+    G = _printed_ghosts(info["e"])
+    rng = np.random.default_rng(71)
+    wp = 1.3
+    p = O.Params(LAT, 4, 4, 4, collision=O.P_TRT, omega_plus=wp, omega_minus=1.0)
+    for _ in range(6):
+        f = _state(rng)
+        fne = _fneq(info, f)
+        r2 = (O.collide(p, f) - (f - fne)) / (1.0 - wp)
+        want = 0.5 * (fne + fne[opp]) - _wproj(w, G, fne)
+        np.testing.assert_allclose(r2, want, rtol=1e-10, atol=1e-15)
+
+
+@pytest.mark.parametrize("force", [(0.0, 0.0, 0.0), (2e-5, -1e-5, 3e-5)])
+def test_hybrid_differs_from_trt_rlb_by_the_fifth_order_residual(force):
+    """Rmk D3Q27 / App. D3Q27: the hybrid keeps fneq- whole, TRT-RLB keeps only
+    its third-order projection; fneq- = P1 + P3 + P5 and P1 fneq = -F_i/2, so
+    the two post-collision states differ by exactly (1 - w-) P5 fneq, with P5 the
+    projection onto the printed psi^(5) modes; that residual is non-zero and
+    moves no mass, momentum or third-order moment."""
+    info = _info()
+    e, w = info["e"].astype(float), info["w"]
+    psi = _printed_fifth(info["e"])
+    rng = np.random.default_rng(72)
+    wm = 1.6
+    ph = O.Params(LAT, 4, 4, 4, collision=O.P_TRT, omega_plus=1.2, omega_minus=wm, force=force)
+    pr = O.Params(LAT, 4, 4, 4, collision=O.TRT_RLB, omega_plus=1.2, omega_minus=wm, force=force)
+    _, H3 = O.hermite(LAT)
+    for _ in range(6):
+        f = _state(rng)
+        d = O.collide(ph, f) - O.collide(pr, f)
+        p5 = _wproj(w, psi, _fneq(info, f, force))
+        np.testing.assert_allclose(d, (1.0 - wm) * p5, rtol=1e-9, atol=1e-16)
+        np.testing.assert_allclose(O.fifth_order_projection(LAT, _fneq(info, f, force)), p5,
+                                   rtol=1e-10, atol=1e-17)
+        assert np.max(np.abs(d)) > 1e-6
+        assert abs(d.sum()) < 1e-16
+        np.testing.assert_allclose(e.T @ d, 0.0, atol=1e-16)
+        np.testing.assert_allclose(np.einsum("iabc,i->abc", H3, d), 0.0, atol=1e-16)
+
+
+def test_fifth_order_modes_reach_axial_and_face_velocities():
+    """The appendix says the psi^(5) modes are non-zero only at body diagonals;
+    the printed formula is not: psi^(5,x) = 1/9 at (1, 0, 0) and -2/9 at
+    (1, 1, 0).  The formula is taken as the definition (it is the complement of
+    span{H1, H3} in the antisymmetric subspace, as the rank test shows)."""
+    info = _info()
+    psi = _printed_fifth(info["e"])
+    idx = {tuple(v): i for i, v in enumerate(info["e"])}
+    assert psi[0, idx[(1, 0, 0)]] == pytest.approx(1 / 9)
+    assert psi[0, idx[(1, 1, 0)]] == pytest.approx(-2 / 9)
+
+
+@pytest.mark.parametrize("coll", [O.P_TRT, O.TRT, O.TRT_RLB])
+def test_collision_conserves_and_relaxes_to_equilibrium(coll):
+    """Mass exact, momentum gains F exactly; an equilibrium state is a fixed point."""
+    info = _info()
+    e = info["e"].astype(float)
+    rng = np.random.default_rng(73)
+    F = np.array([1e-5, -2e-5, 3e-5])
+    p = O.Params(LAT, 4, 4, 4, collision=coll, omega_plus=1.1, omega_minus=1.5, force=tuple(F))
+    for _ in range(4):
+        f = _state(rng)
+        fs = O.collide(p, f)
+        assert fs.sum() == pytest.approx(f.sum(), rel=1e-15)
+        np.testing.assert_allclose(e.T @ fs, e.T @ f + F, atol=1e-15)
+    p0 = O.Params(LAT, 4, 4, 4, collision=coll, omega_plus=1.1, omega_minus=1.5)
+    feq = O.equilibrium(LAT, 1.01, (0.03, -0.02, 0.05))
+    np.testing.assert_allclose(O.collide(p0, feq), feq, rtol=1e-14)
+
+
+def test_poiseuille_d3q27_channel_exact_at_magic_lambda():
+    """Force-driven channel on D3Q27 (walls normal to y): the TRT-family schemes
+    give the discrete parabola to roundoff at Lambda = 3/16 (Sec. 3.3), not at 1/4."""
+    import math
+    import workloads as W
+    N, uc, nu = 12, 0.05, 0.4
+
+    def run(Lam, coll):
+        wp, wm = O.rates(nu=nu, Lambda=Lam)
+        g = 8.0 * nu * uc / N ** 2
+        p = O.Params(LAT, 3, N, 3, collision=coll, omega_plus=wp, omega_minus=wm,
+                     force=(g, 0.0, 0.0), periodic=(1, 0, 1))
+        rho, u = W.channel_at_rest(p.shape, 3)
+        f = O.step(p, O.init_equilibrium(p, rho, u), int(34.0 / (math.pi ** 2 * nu / N ** 2)))
+        _, uu = O.macros(p, f)
+        ux = np.moveaxis(uu[0], 1, -1).reshape(-1, N)
+        return O.l2(ux, np.broadcast_to(W.poiseuille_profile(N, uc), ux.shape)), uu
+
+    for coll in (O.P_TRT, O.TRT):
+        l2, uu = run(3.0 / 16.0, coll)
+        assert l2 < 1e-12
+        assert np.max(np.abs(uu[1:])) < 1e-13
+    assert run(0.25, O.P_TRT)[0] > 1e-4
