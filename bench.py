@@ -38,7 +38,8 @@ if ROOT not in sys.path:
 METRIC = "P-TRT MLUPS & % HBM roofline (D3Q19/D2Q9); FP16-store vs FP32 at set error"
 BYTES_PER_NODE = {("D2Q9", "F64"): 144, ("D2Q9", "F32"): 72, ("D2Q9", "F16"): 36,
                   ("D2Q9", "BF16"): 36, ("D3Q19", "F64"): 304, ("D3Q19", "F32"): 152,
-                  ("D3Q19", "F16"): 76, ("D3Q19", "BF16"): 76}
+                  ("D3Q19", "F16"): 76, ("D3Q19", "BF16"): 76, ("D3Q27", "F64"): 432,
+                  ("D3Q27", "F32"): 216, ("D3Q27", "F16"): 108, ("D3Q27", "BF16"): 108}
 PROFILE = os.path.join(ROOT, "profiles", "stream_collide_d2q9_f32_4096.md")
 
 
@@ -265,14 +266,14 @@ def workload_fields(kind: str, n: int):
 def make_lattice(lat: str, n: int, storage: str, collision: str = "P_TRT", layout: str = "AB",
                  tau_minus: float | None = None):
     """D2Q9: double shear layer, Re = U0 N / nu = 1e5, 1/tau- = 1.6 (the stability
-    optimum of Sec. 3.1).  D3Q19: Taylor-Green vortex at Re = 1600 (L = N / 2 pi),
-    Lambda = 1/4 unless tau_minus is given."""
+    optimum of Sec. 3.1).  D3Q19 / D3Q27: Taylor-Green vortex at Re = 1600
+    (L = N / 2 pi), Lambda = 1/4 unless tau_minus is given."""
     from paper_2602_06686_gb300 import Lattice
     if lat == "D2Q9":
         return Lattice(lattice="D2Q9", nx=n, ny=n, nz=1, nu=0.1 * n / 1e5, tau_minus=1 / 1.6,
                        collision=collision, storage=storage, layout=layout)
     rates = dict(tau_minus=tau_minus) if tau_minus else dict(Lambda=0.25)
-    return Lattice(lattice="D3Q19", nx=n, ny=n, nz=n, nu=0.05 * n / (2 * math.pi * 1600),
+    return Lattice(lattice=lat, nx=n, ny=n, nz=n, nu=0.05 * n / (2 * math.pi * 1600),
                    collision=collision, storage=storage, layout=layout, **rates)
 
 
@@ -783,7 +784,7 @@ def run_case(args):
                     collision=coll, storage=st, layout=layout)
         rho, u = W.double_shear_rect(nx, ny)
     else:
-        g = Lattice(lattice="D3Q19", nx=nx, ny=ny, nz=nz, nu=0.05 * nx / (2 * math.pi * 1600),
+        g = Lattice(lattice=lat, nx=nx, ny=ny, nz=nz, nu=0.05 * nx / (2 * math.pi * 1600),
                     Lambda=0.25, collision=coll, storage=st, layout=layout)
         rho, u = W.channel_at_rest((nz, ny, nx), 3)
         u[0] = 0.02
@@ -912,6 +913,10 @@ def run_ours(args):
             ("d3q19_f64", lambda: secondary("D3Q19", 384, "F64", "taylor_green_3d", peak)),
             ("d3q19_f32_aa",
              lambda: secondary("D3Q19", 384, "F32", "taylor_green_3d", peak, layout="AA")),
+            ("d3q27_f32", lambda: secondary("D3Q27", 384, "F32", "taylor_green_3d", peak)),
+            ("d3q27_f16", lambda: secondary("D3Q27", 384, "F16", "taylor_green_3d", peak)),
+            ("d3q27_trt_rlb_f32",
+             lambda: secondary("D3Q27", 384, "F32", "taylor_green_3d", peak, "TRT_RLB")),
             ("d2q9_f32_scheme2",
              lambda: secondary("D2Q9", n, "F32", "double_shear", peak, scheme=2)),
             ("d3q19_f32_scheme2",

@@ -32,6 +32,12 @@
  *         7..10 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); 11..14 = (1,0,1),(-1,0,-1),
  *         (1,0,-1),(-1,0,1); 15..18 = (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);
  *         w = 1/3, 1/18, 1/36.
+ *   D3Q27 (App. D3Q27, order and weights not printed): 0..18 as D3Q19; 19..26 =
+ *         (1,1,1),(-1,-1,-1),(1,1,-1),(-1,-1,1),(1,-1,1),(-1,1,-1),(-1,1,1),(1,-1,-1);
+ *         w = 8/27, 2/27, 1/54, 1/216 (products of the D1Q3 weights).
+ *         P-TRT on D3Q27 is the hybrid of Eq. PTRT_D3Q27: R2 the tensor (Hermite)
+ *         projection, R3 = fneq- + F_i/2 (the fifth-order residual kept); TRT-RLB
+ *         is the exact operator of the appendix (the residual removed).
  *
  * Conventions common to every call:
  *   - Device buffers are allocated by the caller and borrowed by the library
@@ -69,7 +75,7 @@ extern "C" {
 #define LBM_ERR_STATE (-6)       /* call out of order (e.g. buffers not bound) */
 #define LBM_ERR_ALIGN (-7)       /* a buffer is not 256-byte aligned */
 
-typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
 typedef enum {
   LBM_TRT = 0,
   LBM_TRT_RLB = 1,

@@ -47,8 +47,10 @@ struct BVariant {
 std::vector<BVariant> batch_variants(const Ops* ops) {
   std::vector<BVariant> v;
   if (ops->batch_tma)
-    for (int X : kTmaWidths)
+    for (int X : kTmaWidths) {
+      if (ops->Q == 27 && X != 256) continue;  // D3Q27 keeps one tile width
       for (int d : kTmaDepths) v.push_back(BVariant{1, 0, 0, X, d});
+    }
   for (int k = 0; k < kNumShapes; ++k) v.push_back(BVariant{0, kShapes[k][0], kShapes[k][1], 0, 0});
   return v;
 }

@@ -41,8 +41,9 @@ int cuda_check(cudaError_t e, const char* what) {
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
 
 const Ops* pick_ops(int lattice, int storage) {
-  static const Ops* (*table[2][4])() = {{ops_d2q9_f64, ops_d2q9_f32, ops_d2q9_f16, ops_d2q9_bf16},
-                                       {ops_d3q19_f64, ops_d3q19_f32, ops_d3q19_f16, ops_d3q19_bf16}};
+  static const Ops* (*table[3][4])() = {{ops_d2q9_f64, ops_d2q9_f32, ops_d2q9_f16, ops_d2q9_bf16},
+                                       {ops_d3q19_f64, ops_d3q19_f32, ops_d3q19_f16, ops_d3q19_bf16},
+                                       {ops_d3q27_f64, ops_d3q27_f32, ops_d3q27_f16, ops_d3q27_bf16}};
   return table[lattice][storage]();
 }
 
@@ -54,7 +55,8 @@ namespace lbm {
 
 int plan(const lbm_params* p, Plan* out) {
   if (!p) return fail(LBM_ERR_ARG, "params is NULL");
-  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return fail(LBM_ERR_ARG, "bad lattice");
+  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19 && p->lattice != LBM_D3Q27)
+    return fail(LBM_ERR_ARG, "bad lattice");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_ERR_ARG, "extent must be >= 1");
   if (p->lattice == LBM_D2Q9 && p->nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
   if (p->ny > 65535 * 8 || p->nz > 65535) return fail(LBM_ERR_ARG, "extent too large");
@@ -77,7 +79,7 @@ int plan(const lbm_params* p, Plan* out) {
   if (!(tm > 0.5) || !isfinite(tm)) return fail(LBM_ERR_ARG, "tau_minus must be > 1/2");
   Plan r{};
   r.p = *p;
-  r.Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+  r.Q = p->lattice == LBM_D2Q9 ? 9 : (p->lattice == LBM_D3Q19 ? 19 : 27);
   r.D = p->lattice == LBM_D2Q9 ? 2 : 3;
   r.esize = storage_bytes(p->storage);
   const int per_vec = 16 / r.esize;
@@ -113,8 +115,10 @@ int plan(const lbm_params* p, Plan* out) {
   r.force = p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0;
   if (p->lattice == LBM_D2Q9)
     fill_coef<D2Q9>(p->rho0, wp, wmk, r.kernel_collision, p->force, &r.coef);
-  else
+  else if (p->lattice == LBM_D3Q19)
     fill_coef<D3Q19>(p->rho0, wp, wmk, r.kernel_collision, p->force, &r.coef);
+  else
+    fill_coef<D3Q27>(p->rho0, wp, wmk, r.kernel_collision, p->force, &r.coef);
   *out = r;
   return LBM_OK;
 }

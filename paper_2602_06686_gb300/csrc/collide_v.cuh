@@ -161,7 +161,7 @@ struct Ar<float> : ArHost<float> {
 // Per-launch constants (computed on the host in FP64, stored in the arithmetic
 // precision).  The force terms are compiled out when the force is zero
 // (FORCE = false).  Per-direction entries are used at pair representatives.
-constexpr int kQMax = 19;
+constexpr int kQMax = 27;
 template <typename S>
 struct CoefV {
   S rho0;
@@ -184,6 +184,15 @@ struct GhostT<D2Q9> {
   __host__ __device__ static constexpr int G(int, int i) { return i == 0 ? 1 : (i <= 4 ? -2 : 4); }
   // phi = G/9, N = 4/81 -> s^2/N = 1/4
   __host__ __device__ static constexpr double coef(int) { return 0.25; }
+};
+
+// D3Q27 P-TRT takes the tensor projection (the hybrid), so its ghost table is
+// never read; TRT, which shares the pair branch, needs only NG.
+template <>
+struct GhostT<D3Q27> {
+  static constexpr int NG = 1;
+  __host__ __device__ static constexpr int G(int, int) { return 0; }
+  __host__ __device__ static constexpr double coef(int) { return 0.0; }
 };
 
 template <>
@@ -281,8 +290,9 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
   const unsigned badmask = A::bad(rho, usq);
 
   // per-node scalars
-  const V rho36 = A::mul(rho, A::c(1.0 / 36.0));
-  const V drho36 = A::mul(drho, A::c(1.0 / 36.0));
+  // rho w_i and drho w_i as (rho / kWDen) * wnum_i (one multiply less when wnum_i = 1)
+  const V rho36 = A::mul(rho, A::c(1.0 / L::kWDen));
+  const V drho36 = A::mul(drho, A::c(1.0 / L::kWDen));
   const V musq15 = A::mul(usq, A::c(-1.5));
   const V k3 = A::fma(usq, A::c(-4.5), A::c(3.0));
   V uF = A::c(0.0);
@@ -296,7 +306,11 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
   const V feq0 = A::mul(A::c(L::w(0)), A::fma(rho, musq15, drho));
   const V np0 = A::sub(g[0], feq0);
 
-  if constexpr (COLL != C_TRT_RLB) {
+  // D3Q27 P-TRT is the hybrid of Eq. PTRT_D3Q27: the tensor projection for the
+  // second-order term (N_G = 7 > M_2 = 6), fneq- for the third; it takes the
+  // Hermite branch below.
+  constexpr bool kHybrid = COLL == C_P_TRT && L::Q == 27;
+  if constexpr (COLL != C_TRT_RLB && !kHybrid) {
     // TRT and P-TRT need no moment of fneq but the ghost moments, so each pair
     // is finished in one pass (few values live at once).  The ghost moments
     // are taken from the populations: the ghost vectors are w-orthogonal to
@@ -335,7 +349,7 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (!is_pair_rep<L>(i)) continue;
-      const int w36 = L::w36(i);
+      const int w36 = L::wnum(i);
       const V eu = edot<L, V>(i, u);
       const V q = A::mul(eu, eu);
       const V t = A::fma(A::c(4.5), q, musq15);
@@ -373,7 +387,7 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (!is_pair_rep<L>(i)) continue;
-      const int w36 = L::w36(i);
+      const int w36 = L::wnum(i);
       const V eu = edot<L, V>(i, u);
       const V q = A::mul(eu, eu);
       const V t = A::fma(A::c(4.5), q, musq15);
@@ -442,7 +456,56 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
 
     // ---- antisymmetric relaxation target R3 and post-collision
     V r3[Q];
-    {
+    if constexpr (kHybrid) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if (is_pair_rep<L>(i)) r3[i] = nm[i];
+    } else if constexpr (L::Q == 27) {
+      // D3Q27 TRT-RLB: the seven third-order modes m_ab = e_a (e_b^2 - cs^2)
+      // (a != b, norm 2 cs^6) and m_xyz = e_x e_y e_z (norm cs^6) are
+      // w-orthogonal on the tensor-product lattice; A_k = sum_i m_k,i fneq_i
+      // = sum over pairs of 2 m_k,i nm_i, R3_i = w_i sum_k m_k,i A_k / N_k.
+      constexpr int kModes = 7;
+      auto mode = [](int k, int i) constexpr -> double {
+        if (k == 6) return double(ecomp<L>(i, 0) * ecomp<L>(i, 1) * ecomp<L>(i, 2));
+        const int a = k / 2, b = (a + 1 + (k & 1)) % 3;
+        const int ea = ecomp<L>(i, a), eb = ecomp<L>(i, b);
+        return ea * (eb * eb - 1.0 / 3.0);
+      };
+      V Am[kModes];
+      bool ai[kModes];
+#pragma unroll
+      for (int k = 0; k < kModes; ++k) {
+        Am[k] = A::c(0.0);
+        ai[k] = false;
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+#pragma unroll
+        for (int k = 0; k < kModes; ++k) {
+          const double m = mode(k, i);
+          if (m == 0.0) continue;
+          Am[k] = ai[k] ? A::fma(A::c(2.0 * m), nm[i], Am[k]) : A::mul(A::c(2.0 * m), nm[i]);
+          ai[k] = true;
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!is_pair_rep<L>(i)) continue;
+        V h = A::c(0.0);
+        bool hi = false;
+#pragma unroll
+        for (int k = 0; k < kModes; ++k) {
+          const double m = mode(k, i);
+          if (m == 0.0) continue;
+          const double cf = (k == 6 ? 27.0 : 13.5) * L::w(i) * m;
+          h = hi ? A::fma(A::c(cf), Am[k], h) : A::mul(A::c(cf), Am[k]);
+          hi = true;
+        }
+        r3[i] = h;
+      }
+    } else {
       // fneq_i - fneq_ibar = 2 nm_i; modes m_ab = e_a (e_b^2 - cs^2)
       auto mode = [](int a, int b, int i) constexpr -> double {
         const int ea = ecomp<L>(i, a), eb = ecomp<L>(i, b);

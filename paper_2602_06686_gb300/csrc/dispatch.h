@@ -182,6 +182,10 @@ const Ops* ops_d3q19_f64();
 const Ops* ops_d3q19_f32();
 const Ops* ops_d3q19_f16();
 const Ops* ops_d3q19_bf16();
+const Ops* ops_d3q27_f64();
+const Ops* ops_d3q27_f32();
+const Ops* ops_d3q27_f16();
+const Ops* ops_d3q27_bf16();
 
 // Generic FP64 reductions over macroscopic fields (diag.cu).
 struct DiagLaunch {

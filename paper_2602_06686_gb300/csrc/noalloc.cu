@@ -70,8 +70,9 @@ __global__ void k_noalloc_finish(double* out, long long step) {
 }
 
 const Ops* ops_for(int lattice, int storage) {
-  static const Ops* (*table[2][4])() = {{ops_d2q9_f64, ops_d2q9_f32, ops_d2q9_f16, ops_d2q9_bf16},
-                                       {ops_d3q19_f64, ops_d3q19_f32, ops_d3q19_f16, ops_d3q19_bf16}};
+  static const Ops* (*table[3][4])() = {{ops_d2q9_f64, ops_d2q9_f32, ops_d2q9_f16, ops_d2q9_bf16},
+                                       {ops_d3q19_f64, ops_d3q19_f32, ops_d3q19_f16, ops_d3q19_bf16},
+                                       {ops_d3q27_f64, ops_d3q27_f32, ops_d3q27_f16, ops_d3q27_bf16}};
   return table[lattice][storage]();
 }
 

@@ -1,0 +1,3 @@
+// Fused update and auxiliary kernels for D3Q27 with f64 storage.
+#include "tu_impl.cuh"
+LBM_DEFINE_OPS(ops_d3q27_f64, D3Q27, StF64)

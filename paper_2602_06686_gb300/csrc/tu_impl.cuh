@@ -591,7 +591,15 @@ struct TU {
 
   // ---- pipelined bulk-copy kernel (kind 1)
   static constexpr bool kPack = sizeof(R) == 4;
+  // D3Q27 keeps one tile width (256 packed, 128 FP64): its 27-plane kernels
+  // are the slowest to compile, and the width sweep gains little there.
+  static constexpr bool kOneTile = L::Q == 27;
+  // register kernels: at most 2 nodes per thread on D3Q27 (54 populations in
+  // flight per thread already)
+  static constexpr int kMaxNV = L::Q == 27 ? 2 : 8;
+  static constexpr int kTile27 = kPack ? 256 : 128;
   static bool tma_width_ok(int X) {
+    if (kOneTile) return X == kTile27;
     return kPack ? (X == 256 || X == 384 || X == 512) : (X == 128 || X == 192 || X == 256);
   }
   static size_t tma_smem(int X, int stages) {
@@ -664,7 +672,9 @@ struct TU {
 
   template <int COLL, bool FORCE>
   static cudaError_t go_tma(const StepLaunch& s) {
-    if constexpr (kPack) {
+    if constexpr (kOneTile) {
+      if (s.v.X == kTile27) return go_tma_x<COLL, FORCE, kTile27>(s);
+    } else if constexpr (kPack) {
       switch (s.v.X) {
         case 256:
           return go_tma_x<COLL, FORCE, 256>(s);
@@ -805,12 +815,16 @@ struct TU {
   }
   static bool s2_tma_ok(const StepLaunch& s) {
     constexpr int H = 16 / (int)sizeof(T);
-    return s.mask == nullptr && s.g.nx % H == 0 && s.g.nx >= 2 * H;
+    // the producer warp copies one plane or Phi row per lane
+    constexpr bool lanes = L::Q + TmaPhi<L, R, 128>::kRows <= 32;
+    return lanes && s.mask == nullptr && s.g.nx % H == 0 && s.g.nx >= 2 * H;
   }
 
   template <int COLL, bool FORCE>
   static cudaError_t go_s2(const StepLaunch& s) {
-    if (s2_tma_ok(s)) return go_s2_tma<COLL, FORCE>(s);
+    if constexpr (L::Q + TmaPhi<L, R, 128>::kRows <= 32) {
+      if (s2_tma_ok(s)) return go_s2_tma<COLL, FORCE>(s);
+    }
     const dim3 grid((unsigned)((long long)s.g.ny * s.g.nz), (unsigned)((s.g.nx + 255) / 256));
     R* phi = static_cast<R*>(s.phi);
     StepArgs<R> a = args(s);
@@ -850,10 +864,10 @@ struct TU {
         if constexpr (2 * sizeof(T) <= 16) return step_nv<2>(s);
         break;
       case 4:
-        if constexpr (4 * sizeof(T) <= 16) return step_nv<4>(s);
+        if constexpr (4 * sizeof(T) <= 16 && 4 <= kMaxNV) return step_nv<4>(s);
         break;
       case 8:
-        if constexpr (8 * sizeof(T) <= 16) return step_nv<8>(s);
+        if constexpr (8 * sizeof(T) <= 16 && 8 <= kMaxNV) return step_nv<8>(s);
         break;
     }
     return cudaErrorInvalidValue;
@@ -956,7 +970,9 @@ struct TU {
   template <int COLL, bool FORCE>
   static void* batch_tma_kernel_cf(int X) {
     if constexpr (kPack) {
-      if (X == 128) return (void*)&k_batch_tma<L, COLL, S, FORCE, 128>;
+      if constexpr (!kOneTile) {
+        if (X == 128) return (void*)&k_batch_tma<L, COLL, S, FORCE, 128>;
+      }
       if (X == 256) return (void*)&k_batch_tma<L, COLL, S, FORCE, 256>;
     }
     return nullptr;
@@ -1029,7 +1045,7 @@ struct TU {
       r.D = L::D;
       r.esize = sizeof(T);
       int n = 0;
-      for (int nv = 1; nv <= 8; nv *= 2)
+      for (int nv = 1; nv <= kMaxNV; nv *= 2)
         if (nv * (int)sizeof(T) <= 16) r.nvs[n++] = nv;
       r.n_nv = n;
       r.step = &step;

@@ -14,12 +14,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liblbm.so")
 
-LATTICES = {"D2Q9": 0, "D3Q19": 1}
+LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
 COLLISIONS = {"TRT": 0, "TRT_RLB": 1, "P_TRT": 2, "BGK": 3, "RLB": 4}
 STORAGES = {"F64": 0, "F32": 1, "F16": 2, "BF16": 3}
 LAYOUTS = {"AB": 0, "AA": 1}
-Q_OF = {0: 9, 1: 19}
-D_OF = {0: 2, 1: 3}
+Q_OF = {0: 9, 1: 19, 2: 27}
+D_OF = {0: 2, 1: 3, 2: 3}
 
 LBM_OK = 0
 LBM_ERR_DIVERGED = -3

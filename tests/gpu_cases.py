@@ -5,7 +5,7 @@ import numpy as np
 import oracle as O
 
 COLL_NAMES = {O.TRT: "TRT", O.TRT_RLB: "TRT_RLB", O.P_TRT: "P_TRT", O.BGK: "BGK", O.RLB: "RLB"}
-LAT_NAMES = {O.D2Q9: "D2Q9", O.D3Q19: "D3Q19"}
+LAT_NAMES = {O.D2Q9: "D2Q9", O.D3Q19: "D3Q19", O.D3Q27: "D3Q27"}
 
 
 def gpu_lattice(lat, shape, coll, nu, Lam, storage="F64", force=(0.0, 0.0, 0.0),
