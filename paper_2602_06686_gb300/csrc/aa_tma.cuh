@@ -24,7 +24,7 @@
 namespace lbm {
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, bool ODD>
-__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S>())
+__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L, S>())
     k_step_aa_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;

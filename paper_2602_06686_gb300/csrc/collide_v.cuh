@@ -307,10 +307,13 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
   const V np0 = A::sub(g[0], feq0);
 
   // D3Q27 P-TRT is the hybrid of Eq. PTRT_D3Q27: the tensor projection for the
-  // second-order term (N_G = 7 > M_2 = 6), fneq- for the third; it takes the
-  // Hermite branch below.
+  // second-order term (N_G = 7 > M_2 = 6), fneq- for the third.  It shares the
+  // one-pass pair branch: the second-order Hermite moments of fneq come from
+  // the pair sums, A2_ab = sum_i e_a e_b g_i - rho u_a u_b - cs^2 drho delta_ab
+  // (the second moment of f_eq is rho u u + rho cs^2 delta, that of the shift
+  // rho0 cs^2 delta), and R2_i = 4.5 w_i H2_i : A2.
   constexpr bool kHybrid = COLL == C_P_TRT && L::Q == 27;
-  if constexpr (COLL != C_TRT_RLB && !kHybrid) {
+  if constexpr (COLL != C_TRT_RLB) {
     // TRT and P-TRT need no moment of fneq but the ghost moments, so each pair
     // is finished in one pass (few values live at once).  The ghost moments
     // are taken from the populations: the ghost vectors are w-orthogonal to
@@ -318,10 +321,43 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
     // the shift w_i rho0, so sum_j G(k,j) fneq_j = sum_j G(k,j) g_j exactly
     // (up to rounding), with g_i + g_ibar = s_i.
     using Gh = GhostT<L>;
-    constexpr int NG = COLL == C_P_TRT ? Gh::NG : 1;
+    constexpr int NG = (COLL == C_P_TRT && !kHybrid) ? Gh::NG : 1;
     V m[NG];
     V r20 = np0;
-    if constexpr (COLL == C_P_TRT) {
+    V A2d[3], A2o[3];  // hybrid: diagonal xx, yy, zz and off-diagonal xy, xz, yz
+    if constexpr (kHybrid) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        bool id = false;
+        A2d[a] = A::c(0.0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i) || ecomp<L>(i, a) == 0) continue;
+          A2d[a] = id ? A::add(A2d[a], s[i]) : s[i];
+          id = true;
+        }
+        A2d[a] = A::fma(A::mul(A::c(-1.0), rho), A::mul(u[a], u[a]), A2d[a]);
+        A2d[a] = A::fma(A::c(-1.0 / 3.0), drho, A2d[a]);
+      }
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+        bool io = false;
+        A2o[o] = A::c(0.0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!is_pair_rep<L>(i)) continue;
+          const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+          if (eab == 0) continue;
+          A2o[o] = io ? (eab > 0 ? A::add(A2o[o], s[i]) : A::sub(A2o[o], s[i]))
+                      : (eab > 0 ? s[i] : A::sub(A::c(0.0), s[i]));
+          io = true;
+        }
+        A2o[o] = A::fma(A::mul(A::c(-1.0), rho), A::mul(u[a], u[b]), A2o[o]);
+      }
+      r20 = A::mul(A::c(4.5 * L::w(0) * (-1.0 / 3.0)), A::add(A::add(A2d[0], A2d[1]), A2d[2]));
+    }
+    if constexpr (COLL == C_P_TRT && !kHybrid) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) {
         V acc = Gh::G(k, 0) == 0 ? A::c(0.0) : A::mul(A::c(double(Gh::G(k, 0))), g[0]);
@@ -359,7 +395,18 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
       const V fs = A::fma(wr, t, wd);              // symmetric part of the shifted f_eq
       const V fa = A::mul(A::mul(wr, eu), t2);     // antisymmetric part
       V r2 = A::sub(A::mul(A::c(0.5), s[i]), fs);  // fneq+
-      if constexpr (COLL == C_P_TRT) {
+      if constexpr (kHybrid) {
+        V h = A::mul(A::c(ecomp<L>(i, 0) * ecomp<L>(i, 0) - 1.0 / 3.0), A2d[0]);
+#pragma unroll
+        for (int a = 1; a < 3; ++a) h = A::fma(A::c(ecomp<L>(i, a) * ecomp<L>(i, a) - 1.0 / 3.0), A2d[a], h);
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+          const int eab = ecomp<L>(i, a) * ecomp<L>(i, b);
+          if (eab != 0) h = A::fma(A::c(2.0 * eab), A2o[o], h);
+        }
+        r2 = A::mul(A::c(4.5 * L::w(i)), h);
+      } else if constexpr (COLL == C_P_TRT) {
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
           if (Gh::G(k, i) == 0) continue;
@@ -456,11 +503,7 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
 
     // ---- antisymmetric relaxation target R3 and post-collision
     V r3[Q];
-    if constexpr (kHybrid) {
-#pragma unroll
-      for (int i = 1; i < Q; ++i)
-        if (is_pair_rep<L>(i)) r3[i] = nm[i];
-    } else if constexpr (L::Q == 27) {
+    if constexpr (L::Q == 27) {
       // D3Q27 TRT-RLB: the seven third-order modes m_ab = e_a (e_b^2 - cs^2)
       // (a != b, norm 2 cs^6) and m_xyz = e_x e_y e_z (norm cs^6) are
       // w-orthogonal on the tensor-product lattice; A_k = sum_i m_k,i fneq_i

@@ -289,13 +289,16 @@ __device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R
 // 16-bit storage (the collision is then the limiter and more warps hide it), 2
 // for FP32, none for FP64 (whose collision needs the registers).  Measured on
 // GB300: +6% (D3Q19 FP16) and +11% (D2Q9 FP32) over no hint.
-template <class S>
+// D3Q27 FP32 asks for 3: at two blocks its 160-thread blocks leave the SM
+// short of consumer warps (occupancy, not registers, limits it).
+template <class L, class S>
 constexpr int tma_min_blocks() {
+  if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : 3;
   return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
 }
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, int MODE = 0>
-__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<S>())
+__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L, S>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
