@@ -82,6 +82,8 @@ def test_sequential_mode_and_tile_shapes_agree():
     ("D2Q9", "BF16", (0, 1, 1), False),   # walls in x (row ends read from HBM)
     ("D3Q19", "F32", (0, 1, 0), True),    # walls in x and z
     ("D3Q19", "F16", (1, 1, 1), False),
+    ("D3Q27", "F32", (1, 0, 1), True),    # walls in y
+    ("D3Q27", "BF16", (0, 1, 1), False),
 ])
 def test_every_batch_variant_equals_single_runs(lat, storage, periodic, forced):
     """Every variant of the batched kernel (pipelined and register tiles, any
@@ -96,7 +98,7 @@ def test_every_batch_variant_equals_single_runs(lat, storage, periodic, forced):
             nx, ny, nz = int(rng.integers(20, 140)), int(rng.integers(6, 40)), 1
         else:
             nx, ny, nz = int(rng.integers(9, 70)), int(rng.integers(4, 12)), int(rng.integers(3, 9))
-        F = (2e-5 * (k % 2), -1e-5 * (k % 2), 1e-5 * (k % 2) if lat == "D3Q19" else 0.0)
+        F = (2e-5 * (k % 2), -1e-5 * (k % 2), 1e-5 * (k % 2) if lat != "D2Q9" else 0.0)
         specs.append(dict(lattice=lat, nx=nx, ny=ny, nz=nz, nu=0.02 + 0.01 * k, Lambda=3 / 16,
                           collision="P_TRT", storage=storage, periodic=periodic,
                           force=F if forced else (0.0, 0.0, 0.0)))
