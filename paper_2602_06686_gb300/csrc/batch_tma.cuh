@@ -13,8 +13,10 @@
 //     mbarrier phases run on across steps.
 // Extents need not be multiples of the 16-byte halo: a row copy is rounded up
 // into the row's pitch padding (never read back), and where a periodic row end
-// is not 16-byte aligned the wrap neighbour is read from HBM by the node itself
-// (ld.global.cg: another SM wrote it in the previous step).
+// is not 16-byte aligned the producer also copies, per plane, the aligned
+// 16 bytes that hold the wrap neighbour (x = nx - 1 for the row's first tile,
+// x = 0 for its last) into two side slots of the stage, from which the end
+// nodes read it.
 // Data written in one step by generic stores is read in the next by the bulk
 // copies (the async proxy): the grid barrier orders the two at GPU scope and
 // a proxy fence on both sides of it orders them across the proxies.
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
   uint64_t* empty = full + ST;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + ST);
   T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
-  constexpr long long stage_elems = (long long)L::Q * SLOT;
+  // Q plane slots, then per plane two HT-element side slots (unaligned wraps)
+  constexpr long long stage_elems = (long long)L::Q * SLOT + (long long)L::Q * 2 * HT;
   int* err = &a.bar->err;
 
   if (threadIdx.x == 0) {
@@ -154,6 +157,8 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
         const bool aligned = (w.nx % HT) == 0;
         const bool lwrap = w.per0 && aligned && x0 == 0;
         const bool rwrap = w.per0 && aligned && xe == w.nx;
+        const bool lwrap_u = w.per0 && !aligned && x0 == 0;   // side slot copies
+        const bool rwrap_u = w.per0 && !aligned && xe == w.nx;
         const uint32_t main_bytes = (uint32_t)(hi - lo) * sizeof(T);
         constexpr uint32_t halo_bytes = (uint32_t)HT * sizeof(T);
         const int i = lane;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
         const uint32_t fb = smem_addr(full + s);
         if (lane == 0) {
           const uint32_t nwrap =
-              (uint32_t)(L::Q - __popc(walls)) * ((lwrap ? 1u : 0u) + (rwrap ? 1u : 0u));
+              (uint32_t)(L::Q - __popc(walls)) * ((lwrap || lwrap_u ? 1u : 0u) + (rwrap || rwrap_u ? 1u : 0u));
           mbar_arrive_expect_tx(fb, main_bytes * L::Q + nwrap * halo_bytes);
         }
         __syncwarp();
@@ -196,6 +201,10 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
           if (!wall) {
             if (lwrap) bulk_g2s(smem_addr(slot), rowp + w.nx - HT, halo_bytes, fb);
             if (rwrap) bulk_g2s(smem_addr(slot + HT + (w.nx - x0)), rowp, halo_bytes, fb);
+            // side slots: [0, HT) the aligned chunk holding x = nx - 1, [HT, 2 HT) x = 0..HT-1
+            T* side = ring + s * stage_elems + (long long)L::Q * SLOT + i * 2 * HT;
+            if (lwrap_u) bulk_g2s(smem_addr(side), rowp + (w.nx - 1) / HT * HT, halo_bytes, fb);
+            if (rwrap_u) bulk_g2s(smem_addr(side + HT), rowp, halo_bytes, fb);
           }
         }
         ++issued;
@@ -274,11 +283,9 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
                 // halfway bounce-back at an x wall: the node's own opposite population
                 v[n] = act[n] ? S::dec(ldcg_elem(src + L::opp(i) * w.plane + own + x)) : 0.f;
               } else if (leaves && (w.nx % HT) != 0) {
-                // periodic wrap not held by the ring
-                const int xs = ex == 1 ? w.nx - 1 : 0;
-                v[n] = act[n] ? S::dec(ldcg_elem(src + i * w.plane +
-                                                 ((long long)zs * w.ny + ys) * w.pitch + xs))
-                              : 0.f;
+                // unaligned periodic wrap: from the plane's side slots
+                const T* side = st + (long long)L::Q * SLOT + i * 2 * HT;
+                v[n] = S::dec(ex == 1 ? side[(w.nx - 1) % HT] : side[HT]);
               } else {
                 v[n] = S::dec(slot[j - ex]);
               }

@@ -960,7 +960,8 @@ struct TU {
     const int H = 16 / (int)sizeof(T);
     if ((X != 128 && X != 256) || stages < 2) return 0;
     const size_t head = 128 * ((2 * (size_t)stages * 8 + 4 + 127) / 128);
-    return head + (size_t)stages * L::Q * (size_t)(X + 2 * H) * sizeof(T);
+    // per stage: Q plane slots and 2 HT-element side slots per plane
+    return head + (size_t)stages * L::Q * (size_t)(X + 4 * H) * sizeof(T);
   }
   // Dynamic shared-memory limit set on the batched kernel: enough for the
   // deepest ring of the variant list (4 stages), and below the opt-in maximum
