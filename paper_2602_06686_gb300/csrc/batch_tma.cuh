@@ -233,9 +233,12 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
         T* dst = reinterpret_cast<T*>(dstb + w.off);
         const bool anywall = (!w.per1 && (w.y == 0 || w.y == w.ny - 1)) ||
                              (L::D == 3 && !w.per2 && (w.z == 0 || w.z == w.nz - 1));
-        // tile touches a row end that the ring does not hold (x wall or an
-        // unaligned periodic wrap)
-        const bool xedge = (x0 == 0 || x0 + XT >= w.nx) && (!w.per0 || (w.nx % HT) != 0);
+        // tile touches a row end at an x wall (per-element path), or an
+        // unaligned periodic row end (fast path, the end nodes then take their
+        // wrap neighbours from the side slots)
+        const bool rowend = x0 == 0 || x0 + XT >= w.nx;
+        const bool xedge = rowend && !w.per0;
+        const bool uwrap = rowend && w.per0 && (w.nx % HT) != 0;
         bool act[NPT];
 #pragma unroll
         for (int n = 0; n < NPT; ++n) act[n] = jn[n] < wdt;
@@ -254,6 +257,24 @@ __global__ void __launch_bounds__(TmaShape<XT, true>::kThreads)
               }
             } else {
               g[i] = F2{S::dec(slot[jn[0]]), S::dec(slot[jn[1]])};
+            }
+          }
+          if (uwrap) {
+            const int jend = w.nx - 1 - x0;  // the row's last node, if in this tile
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+              const int ex = L::cx(i);
+              if (ex == 0) continue;
+              const T* side = st + (long long)L::Q * SLOT + i * 2 * HT;
+              const T* src_w = ex == 1 ? side + (w.nx - 1) % HT : side + HT;
+#pragma unroll
+              for (int n = 0; n < NPT; ++n) {
+                const bool end = ex == 1 ? (x0 + jn[n] == 0) : (jn[n] == jend);
+                if (end) {
+                  if (n == 0) g[i].x = S::dec(*src_w);
+                  else g[i].y = S::dec(*src_w);
+                }
+              }
             }
           }
         } else {
