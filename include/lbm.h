@@ -197,7 +197,7 @@ int lbm_velocity_l2(lbm_ctx* ctx, const double* u_ref, double* out);
  * and lbm_macros, lbm_get_populations and lbm_diagnostics report the state with
  * them applied.  A state written directly (lbm_init_equilibrium,
  * lbm_set_populations, lbm_restore at t = 0) is taken as given: the rules act
- * from the first streaming on.  LBM_ERR_UNSUPPORTED for D3Q19 or AA,
+ * from the first streaming on.  LBM_ERR_UNSUPPORTED for D3Q19, D3Q27 or AA,
  * LBM_ERR_ARG for a periodic x axis, nx < 2 or |u_in| >= 1. */
 int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
 
