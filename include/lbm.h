@@ -212,15 +212,17 @@ int lbm_set_open_boundaries(lbm_ctx* ctx, double u_in, double rho_out);
  * one-sided difference where one neighbour is a solid node or beyond a
  * non-periodic edge, 0 where both are.  Scheme 2 runs two launches per step: a
  * pass that stores rho u_a^3 of every node in the scratch buffer's field area,
- * then the update.  Without a solid mask and with rows of whole 16-byte units
- * both run on the pipelined kernel (the update copies the rho u^3 rows a tile
- * needs through its ring) with the tile width and ring depth of the selected
- * pipelined variant, or the widest tile under a register variant; otherwise
- * on one-node-per-thread kernels.  It changes neither the state's layout nor
+ * then the update.  On the A/B layout without a solid mask and with rows of
+ * whole 16-byte units both run on the pipelined kernel (the update copies the
+ * rho u^3 rows a tile needs through its ring) with the tile width and ring
+ * depth of the selected pipelined variant, or the widest tile under a
+ * register variant; otherwise
+ * (a solid mask, the AA layout -- updated in place -- or D3Q27) on
+ * one-node-per-thread kernels.  It changes neither the state's layout nor
  * lbm_macros / lbm_diagnostics.
- * LBM_ERR_ARG for another value; LBM_ERR_UNSUPPORTED for scheme 2 with the AA
- * layout or with open boundaries on (lbm_set_open_boundaries and
- * lbm_momentum_exchange also refuse scheme 2); LBM_ERR_STATE on a batch view. */
+ * LBM_ERR_ARG for another value; LBM_ERR_UNSUPPORTED for scheme 2 with open
+ * boundaries on (lbm_set_open_boundaries and lbm_momentum_exchange also
+ * refuse scheme 2); LBM_ERR_STATE on a batch view. */
 int lbm_set_forcing_scheme(lbm_ctx* ctx, int scheme);
 
 /* Force on the solid nodes by momentum exchange (Sec. 3.4), FP64, into out[3]:

@@ -553,8 +553,6 @@ int lbm_set_forcing_scheme(lbm_ctx* c, int scheme) {
     return LBM_OK;
   }
   if (c->view) return fail(LBM_ERR_STATE, "batch views take forcing scheme 1 only");
-  if (c->pl.p.layout != LBM_LAYOUT_AB)
-    return fail(LBM_ERR_UNSUPPORTED, "forcing scheme 2: A/B layout only");
   if (c->open.on) return fail(LBM_ERR_UNSUPPORTED, "forcing scheme 2 with open boundaries");
   c->scheme = 2;
   return LBM_OK;

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256) k_step_open(const StepArgs<typename S::R>
 // neighbours are fluid nodes (a periodic axis wraps), one-sided where one is
 // solid or beyond a non-periodic edge, zero where both are.
 template <class L, class S>
-__global__ void __launch_bounds__(256) k_phi(const StepArgs<typename S::R> a, typename S::R* phi) {
+__global__ void __launch_bounds__(256) k_phi(const StepArgs<typename S::R> a, int layout,
+                                             int parity, typename S::R* phi) {
   using R = typename S::R;
   using T = typename S::T;
   const Geo& G = a.g;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_phi(const StepArgs<typename S::R> a, ty
   R drho = R(0), j[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const R v = S::dec(src[ab_slot<L>(G, a.mask, q.x, q.y, q.z, i)]);
+    const R v = S::dec(src[state_slot<L>(G, a.mask, layout, parity, q.x, q.y, q.z, i)]);
     drho += v;
     if (L::cx(i)) j[0] += R(L::cx(i)) * v;
     if (L::cy(i)) j[1] += R(L::cy(i)) * v;
@@ -199,6 +200,41 @@ __global__ void __launch_bounds__(256) k_step_s2(const StepArgs<typename S::R> a
     if (L::cy(i)) h += Dg[1];
     if (L::cz(i)) h += Dg[2];
     dst[i * G.plane + own] = S::enc(g[i] + gk * R(L::w(i)) * h);
+  }
+  record_bad(a.flag, a.step, bad);
+}
+
+// The Scheme II update on the AA layout, in place as aa_node: the node reads
+// its slot set through aa_state_slot and writes f*_i + G_i back into it.
+template <class L, int COLL, bool FORCE, class S>
+__global__ void __launch_bounds__(256) k_step_s2_aa(const StepArgs<typename S::R> a, int parity,
+                                                    const typename S::R* __restrict__ phi,
+                                                    typename S::R gk) {
+  using R = typename S::R;
+  using T = typename S::T;
+  const Geo& G = a.g;
+  const RowNode q(G);
+  if (!q.valid || (a.mask && a.mask[q.n])) return;
+  T* buf = static_cast<T*>(a.dst);
+  R g[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i)
+    g[i] = S::dec(buf[aa_state_slot<L>(G, a.mask, parity, q.x, q.y, q.z, i)]);
+  R Dg[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int d = 0; d < L::D; ++d) Dg[d] = phi_grad<L, R>(G, a.mask, phi, d, q.x, q.y, q.z, q.n);
+  const bool bad = collide_v<L, COLL, FORCE, R>(g, a.c) != 0u;
+  const R third = (Dg[0] + Dg[1] + Dg[2]) * R(1.0 / 3.0);
+  const long long own = ((long long)q.z * G.ny + q.y) * G.pitch + q.x;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    R h = -third;
+    if (L::cx(i)) h += Dg[0];
+    if (L::cy(i)) h += Dg[1];
+    if (L::cz(i)) h += Dg[2];
+    const long long slot = parity == 0 ? L::opp(i) * G.plane + own
+                                       : aa_odd_dst<L>(G, a.mask, q.x, q.y, q.z, i);
+    buf[slot] = S::enc(g[i] + gk * R(L::w(i)) * h);
   }
   record_bad(a.flag, a.step, bad);
 }
@@ -823,17 +859,20 @@ struct TU {
   template <int COLL, bool FORCE>
   static cudaError_t go_s2(const StepLaunch& s) {
     if constexpr (L::Q + TmaPhi<L, R, 128>::kRows <= 32) {
-      if (s2_tma_ok(s)) return go_s2_tma<COLL, FORCE>(s);
+      if (s.layout == 0 && s2_tma_ok(s)) return go_s2_tma<COLL, FORCE>(s);
     }
     const dim3 grid((unsigned)((long long)s.g.ny * s.g.nz), (unsigned)((s.g.nx + 255) / 256));
     R* phi = static_cast<R*>(s.phi);
     StepArgs<R> a = args(s);
-    k_phi<L, S><<<grid, 256, 0, s.stream>>>(a, phi);
+    k_phi<L, S><<<grid, 256, 0, s.stream>>>(a, s.layout, s.parity, phi);
     CoefV<double> c = s.c;  // the F_i projection: no symmetric Guo terms
     for (int i = 0; i < kQMax; ++i) c.fe[i] = c.fu[i] = 0.0;
     a.c = coef_cast<R>(c);
     const R gk = R(-4.5 * (1.0 - 0.5 * (1.0 - s.c.cp)));
-    k_step_s2<L, COLL, FORCE, S><<<grid, 256, 0, s.stream>>>(a, phi, gk);
+    if (s.layout == 1)
+      k_step_s2_aa<L, COLL, FORCE, S><<<grid, 256, 0, s.stream>>>(a, s.parity, phi, gk);
+    else
+      k_step_s2<L, COLL, FORCE, S><<<grid, 256, 0, s.stream>>>(a, phi, gk);
     return cudaGetLastError();
   }
   template <int COLL>
@@ -841,7 +880,7 @@ struct TU {
     return s.force ? go_s2<COLL, true>(s) : go_s2<COLL, false>(s);
   }
   static cudaError_t step_s2(const StepLaunch& s) {
-    if (s.layout != 0 || s.phi == nullptr || s.open.on) return cudaErrorInvalidValue;
+    if (s.phi == nullptr || s.open.on) return cudaErrorInvalidValue;
     switch (s.collision) {
       case C_TRT:
         return s2_coll<C_TRT>(s);
