@@ -237,3 +237,19 @@ def test_taylor_green_3d_linear_decay_d3q27():
     f19 = O.init_equilibrium(p19, rho, u)
     r19 = O.diagnostics(p19, O.step(p19, f19, t, nthreads=4))["kinetic_energy"] / d0["kinetic_energy"]
     assert ratio == pytest.approx(r19, rel=5e-3)
+
+
+@pytest.mark.parametrize("coll", [O.P_TRT, O.TRT_RLB])
+@pytest.mark.parametrize("force", [(0.0, 0.0, 0.0), (2e-5, -1e-5, 3e-5)])
+def test_post_collision_ghost_moments_vanish(coll, force):
+    """Eq. collision_PTRT on D3Q27: the hybrid (like TRT-RLB) leaves no ghost
+    content; every printed G1..G7 moment of f* is that of f_eq, i.e. zero
+    (f_eq's symmetric part and the Guo source lie in span{1, H2})."""
+    info = _info()
+    G = _printed_ghosts(info["e"])
+    rng = np.random.default_rng(74)
+    p = O.Params(LAT, 4, 4, 4, collision=coll, omega_plus=1.4, omega_minus=1.1, force=force)
+    for _ in range(4):
+        f = _state(rng)
+        assert np.max(np.abs(G @ f)) > 1e-5  # the input carries ghost content
+        np.testing.assert_allclose(G @ O.collide(p, f), 0.0, atol=1e-15)

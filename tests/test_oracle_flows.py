@@ -155,6 +155,8 @@ def _brute_stream(p, fstar, solid):
     (O.D2Q9, (1, 6, 5), (0, 1, 1)),
     (O.D3Q19, (4, 5, 6), (1, 0, 1)),
     (O.D3Q19, (3, 4, 5), (0, 0, 0)),
+    (O.D3Q27, (3, 4, 5), (1, 0, 1)),
+    (O.D3Q27, (3, 3, 4), (0, 0, 0)),
 ])
 def test_streaming_matches_brute_force(lat, shape, periodic):
     """One oracle step equals node-wise collision (oracle_collide) followed by an
