@@ -50,6 +50,11 @@ def test_buffer_plan(lib):
     assert pop == 19 * plane * 2
     _, scr = buffer_sizes(make_params("D3Q19", 10, 10, 10, nu=0.01, Lambda=0.25))
     assert scr >= 4 * 1000 * 8
+    # D3Q27: 27 planes; the scratch field area also holds the Scheme II rho u^3 field
+    pop, scr = buffer_sizes(make_params("D3Q27", 24, 6, 5, nu=0.01, Lambda=0.25, storage="F32"))
+    plane = ((24 * 6 * 5 + 63) // 64) * 64
+    assert pop == 27 * plane * 4
+    assert scr >= 4 * 24 * 6 * 5 * 8
 
 
 @pytest.mark.parametrize("kw", [
@@ -62,6 +67,7 @@ def test_buffer_plan(lib):
     dict(lattice="D2Q9", nx=8, ny=8, rho0=0.0),
     dict(lattice="D2Q9", nx=8, ny=8, force=(0, 0, 1e-3)),
     dict(lattice="D2Q9", nx=8, ny=8, periodic=(2, 1, 1)),
+    dict(lattice=3, nx=8, ny=8, nz=8),                        # no fourth lattice
 ])
 def test_invalid_parameters_rejected(lib, kw):
     from paper_2602_06686_gb300.lbm import LBMError, buffer_sizes, make_params
