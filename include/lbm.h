@@ -252,17 +252,29 @@ int lbm_status(lbm_ctx* ctx, long long* first_step);
  *               steps since initialisation, pop_b after an odd one), for AA the
  *               single buffer;
  *   solid_mask  device uint8 [nz][ny][nx] or NULL, as bound to the context;
+ *   open_bc     host {u_in, rho_out} of lbm_set_open_boundaries, or NULL.  Pass
+ *               it for a state that the update with open boundaries streamed
+ *               (lbm_diagnostics then applies the inlet and outlet rules to the
+ *               gathered populations); pass NULL for a lattice without open
+ *               boundaries and for a state written directly and not stepped
+ *               since (lbm_init_equilibrium, lbm_set_populations).  The same
+ *               conditions as lbm_set_open_boundaries apply (D2Q9, A/B,
+ *               x non-periodic, |u_in| < 1, rho_out > 0), else LBM_ERR_ARG or
+ *               LBM_ERR_UNSUPPORTED;
  *   steps_done  steps completed since initialisation (selects the AA slot
  *               rule and is stored in out[7]).
- * It allocates nothing: its working memory is one fixed array of about 8.4 MB
- * inside the library, which every GPU that loads the library holds until the
- * process exits.  Lattices of more than 262144 nodes (e.g. 512 x 512, 64^3) are
- * rejected with LBM_ERR_ARG.  The first call on a device looks the array up
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the array, so calls whose
- * work overlaps on the GPU race; the array keeps the last call's contents. */
+ * For the same state it returns the same bits as lbm_diagnostics (the same
+ * kernels and reduction order).  It allocates nothing: its working memory is
+ * one fixed array of about 8.7 MB inside the library, which every GPU that
+ * loads the library holds until the process exits.  Lattices of more than
+ * 262144 nodes (e.g. 512 x 512, 64^3) are rejected with LBM_ERR_ARG.  The first
+ * call in a CUDA context looks the array up (cudaGetSymbolAddress) with that
+ * context current; make that first call before any stream capture.  All calls
+ * on a device share the array, so calls whose work overlaps on the GPU race;
+ * the array keeps the last call's contents. */
 int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_state, const uint8_t* solid_mask,
-                            long long steps_done, double* out, void* cuda_stream);
+                            const double* open_bc, long long steps_done, double* out,
+                            void* cuda_stream);
 
 /* Number of completed time steps since initialisation. */
 int lbm_step_count(const lbm_ctx* ctx, long long* t);

@@ -16,7 +16,13 @@
 // read before the same call has written it, so it needs no clearing between
 // calls; it keeps the contents of the last call.  All calls on a device share
 // it, so calls whose work overlaps on the GPU (on different streams) race.
+//
+// The reduction uses the block count of lbm_diagnostics (one block per row, at
+// most 8 per multiprocessor and kMaxPartials), so that for the same state both
+// entry points sum in the same order and return the same bits.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -28,36 +34,90 @@ using namespace lbm;
 namespace {
 
 constexpr long long kNoAllocMaxNodes = 1LL << 18;  // 262144 nodes, e.g. 512 x 512 or 64^3
-constexpr int kNoAllocBlocks = 1024;               // block partials of the reduction
+constexpr int kNoAllocBlocks = kMaxPartials;       // block partials of the reduction
 constexpr long long kNoAllocDoubles =
     4 * kNoAllocMaxNodes + (long long)kNoAllocBlocks * 8 + 32;  // rho, u[<=3], partials, result
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {nullptr};
+// The array's device address belongs to the CUDA context that loaded the
+// library's module; after a context is destroyed (cudaDeviceReset) and created
+// again the module is loaded anew.  The address is therefore cached per
+// context, keyed by the driver's context id (unique for the process lifetime),
+// and looked up again for a context it has not seen.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the array on the current device, looked up once per device
-// (cudaGetSymbolAddress) with that device current.
+constexpr int kCacheSlots = 64;
+struct CacheSlot {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+std::mutex g_mu;
+CacheSlot g_cache[kCacheSlots];
+int g_cache_used = 0;
+int g_cache_next = 0;  // slot replaced next once the cache is full
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+
+int driver_entry_points() {
+  if (g_get_current && g_get_id) return LBM_OK;
+  void* a = nullptr;
+  void* b = nullptr;
+  cudaDriverEntryPointQueryResult qa, qb;
+  cudaError_t ea = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+  cudaError_t eb = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+  if (ea != cudaSuccess || eb != cudaSuccess || qa != cudaDriverEntryPointSuccess ||
+      qb != cudaDriverEntryPointSuccess || !a || !b)
+    return ctx_fail(LBM_ERR_CUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId unavailable");
+  g_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+  g_get_id = reinterpret_cast<CtxGetIdFn>(b);
+  return LBM_OK;
+}
+
+// Device address of the array in the current context, looked up
+// (cudaGetSymbolAddress) once per context with that context's device current.
 int scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ctx_fail(LBM_ERR_CUDA, "cudaGetDevice failed");
-  if (dev < 0 || dev >= kMaxDevices) return ctx_fail(LBM_ERR_UNSUPPORTED, "device index too large");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      char buf[256];
-      snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
-               cudaGetErrorString(e));
-      return ctx_fail(LBM_ERR_CUDA, buf);
-    }
-    g_ptr[dev] = static_cast<double*>(p);
+  int rc = driver_entry_points();
+  if (rc) return rc;
+  CUcontext ctx = nullptr;
+  if (g_get_current(&ctx) != CUDA_SUCCESS)
+    return ctx_fail(LBM_ERR_CUDA, "cannot query the current CUDA context");
+  if (!ctx) {
+    // no context current in this thread yet: make the device's primary one current
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess || g_get_current(&ctx) != CUDA_SUCCESS || !ctx)
+      return ctx_fail(LBM_ERR_CUDA, "no CUDA context on the current device");
   }
-  *out = g_ptr[dev];
+  unsigned long long id = 0;
+  if (g_get_id(ctx, &id) != CUDA_SUCCESS)
+    return ctx_fail(LBM_ERR_CUDA, "cannot identify the current CUDA context");
+  for (int k = 0; k < g_cache_used; ++k)
+    if (g_cache[k].ctx_id == id) {
+      *out = g_cache[k].ptr;
+      return LBM_OK;
+    }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
+             cudaGetErrorString(e));
+    return ctx_fail(LBM_ERR_CUDA, buf);
+  }
+  int slot = g_cache_used;
+  if (slot < kCacheSlots) {
+    ++g_cache_used;
+  } else {
+    slot = g_cache_next;
+    g_cache_next = (g_cache_next + 1) % kCacheSlots;
+  }
+  g_cache[slot] = CacheSlot{id, static_cast<double*>(p)};
+  *out = static_cast<double*>(p);
   return LBM_OK;
 }
 
@@ -79,8 +139,8 @@ const Ops* ops_for(int lattice, int storage) {
 }  // namespace
 
 extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_state,
-                                       const uint8_t* solid_mask, long long steps_done, double* out,
-                                       void* cuda_stream) {
+                                       const uint8_t* solid_mask, const double* open_bc,
+                                       long long steps_done, double* out, void* cuda_stream) {
   Plan pl;
   int rc = plan(p, &pl);
   if (rc) return rc;
@@ -93,9 +153,26 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_stat
              pl.N, kNoAllocMaxNodes);
     return ctx_fail(LBM_ERR_ARG, buf);
   }
+  OpenBC open{};
+  if (open_bc) {
+    // the same conditions as lbm_set_open_boundaries
+    if (pl.p.lattice != LBM_D2Q9 || pl.p.layout != LBM_LAYOUT_AB)
+      return ctx_fail(LBM_ERR_UNSUPPORTED, "open boundaries: D2Q9 with the A/B layout");
+    if (pl.g.per[0] || pl.p.nx < 2)
+      return ctx_fail(LBM_ERR_ARG, "open boundaries need a non-periodic x axis with nx >= 2");
+    if (!(fabs(open_bc[0]) < 1.0) || !(open_bc[1] > 0.0))
+      return ctx_fail(LBM_ERR_ARG, "open_bc needs |u_in| < 1 and rho_out > 0");
+    open.on = 1;
+    open.u_in = open_bc[0];
+    open.rho_out = open_bc[1];
+  }
   double* base = nullptr;
   rc = scratch_address(&base);
   if (rc) return rc;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return ctx_fail(LBM_ERR_CUDA, "cannot query the multiprocessor count");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   void* fields = base;  // drho [N] and u [D][N] in the arithmetic precision
   double* partials = base + 4 * kNoAllocMaxNodes;
@@ -109,8 +186,12 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_stat
   a.layout = pl.p.layout;
   a.parity = (int)(steps_done & 1);
   a.stream = st;
+  a.open = open;
   const Ops* ops = ops_for(pl.p.lattice, pl.p.storage);
+  // the block rule of lbm_diagnostics
   long long blocks = (long long)pl.p.ny * pl.p.nz;
+  const long long cap = sms > 0 ? 8LL * sms : 1024;
+  if (blocks > cap) blocks = cap;
   if (blocks > kNoAllocBlocks) blocks = kNoAllocBlocks;
   cudaError_t e = ops->diag(a, fields, partials, (int)blocks, out);
   if (e != cudaSuccess) return ctx_fail(LBM_ERR_CUDA, "diagnostics launch failed");

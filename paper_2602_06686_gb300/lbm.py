@@ -119,7 +119,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_batch_set_barrier": ([vp, ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "lbm_batch_launches": ([vp, ll], ctypes.c_int),
         "lbm_batch_destroy": ([vp], ctypes.c_int),
-        "lbm_diagnostics_noalloc": ([pp, vp, vp, ctypes.c_longlong, vp, vp], ctypes.c_int),
+        "lbm_diagnostics_noalloc": ([pp, vp, vp, dp, ctypes.c_longlong, vp, vp], ctypes.c_int),
         "lbm_set_open_boundaries": ([vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
         "lbm_momentum_exchange": ([vp, dp], ctypes.c_int),
         "lbm_set_forcing_scheme": ([vp, ctypes.c_int], ctypes.c_int),
