@@ -46,6 +46,8 @@
 #pragma once
 #include <string.h>
 
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace lbm {
@@ -236,6 +238,23 @@ __device__ __forceinline__ V edot(int i, const V (&v)[3]) {
   return acc;
 }
 
+// x / den for the integer denominator of the weights.  In FP32 arithmetic the
+// reciprocal is split into head + tail (head = 1/den rounded to FP32, tail =
+// the rounding error of the head, itself rounded): fma(x, head, x * tail) is x/den
+// to within the final rounding, with no common relative bias.
+template <typename V>
+__device__ __forceinline__ V wden_div(V x, int den) {
+  using A = Ar<V>;
+  if constexpr (std::is_same<typename A::S, float>::value) {
+    const double inv = 1.0 / den;
+    const float head = float(inv);
+    const float tail = float(inv - double(head));
+    return A::fma(x, A::c(head), A::mul(x, A::c(tail)));
+  } else {
+    return A::mul(x, A::c(1.0 / den));
+  }
+}
+
 // The collision.  Returns a bit mask of the lanes (nodes) that are not finite,
 // have rho <= 0 or |u| > 1.
 template <class L, int COLL, bool FORCE, typename V>
@@ -290,9 +309,18 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
   const unsigned badmask = A::bad(rho, usq);
 
   // per-node scalars
-  // rho w_i and drho w_i as (rho / kWDen) * wnum_i (one multiply less when wnum_i = 1)
-  const V rho36 = A::mul(rho, A::c(1.0 / L::kWDen));
-  const V drho36 = A::mul(drho, A::c(1.0 / L::kWDen));
+  // rho w_i and drho w_i as (rho / kWDen) * wnum_i (one multiply less when wnum_i = 1).
+  // 1/kWDen is not a binary fraction.  Multiplying by its rounded value would
+  // scale every weight by the same (1 + d), so the equilibrium would carry
+  // (1 + d) times the node's momentum, and the antisymmetric relaxation adds
+  // w- d j to the momentum at every step: a drift that compounds over a run
+  // (in FP32, d = 7.5e-9 gains 2.4e-8 of the kinetic energy per step at
+  // w- = 1.6).  The quotient is therefore formed with the constant split into
+  // its rounded head and the tail the rounding dropped, fma(x, head, x tail),
+  // whose error is the final rounding alone (random from node to node).  In
+  // FP64 the same bias is 1e-17 per step and the plain product is kept.
+  const V rho36 = wden_div<V>(rho, L::kWDen);
+  const V drho36 = wden_div<V>(drho, L::kWDen);
   const V musq15 = A::mul(usq, A::c(-1.5));
   const V k3 = A::fma(usq, A::c(-4.5), A::c(3.0));
   V uF = A::c(0.0);
@@ -302,8 +330,11 @@ __device__ __forceinline__ unsigned collide_v(V (&g)[L::Q], const CoefV<typename
     if (L::D == 3) uF = A::fma(u[2], A::c(c.F[2]), uF);
   }
 
-  // rest velocity: f_eq0 - w0 rho0 = w0 (drho - 1.5 rho u^2)
-  const V feq0 = A::mul(A::c(L::w(0)), A::fma(rho, musq15, drho));
+  // rest velocity: f_eq0 - w0 rho0 = w0 (drho - 1.5 rho u^2), with w0 taken as
+  // wnum_0 / kWDen through the same scaled densities as the moving directions:
+  // a separately rounded w0 would make the weights of the equilibrium sum to
+  // 1 + (d0 - d) and move mass by (1 - w+)(d0 - d) w0 1.5 rho u^2 at every step.
+  const V feq0 = A::mul(A::c(double(L::wnum(0))), A::fma(rho36, musq15, drho36));
   const V np0 = A::sub(g[0], feq0);
 
   // D3Q27 P-TRT is the hybrid of Eq. PTRT_D3Q27: the tensor projection for the
