@@ -19,9 +19,18 @@
 // Masked lattices use the register kernels of aa.cuh.
 #pragma once
 #include "aa.cuh"
+#include "dispatch.h"
 #include "tma.cuh"
 
 namespace lbm {
+
+// Destination of one plane's staged row in the odd step: element offset of
+// the destination row (plane and row), and the window [lo, hi) of x that this
+// tile's nodes write there.
+struct alignas(16) AaPlane {
+  long long off;
+  int lo, hi;
+};
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, bool ODD>
 __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L, S>())
@@ -40,11 +49,24 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + ST);
   T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
   constexpr long long stage_elems = (long long)L::Q * SLOT;
+  // odd step: after the ring (128-byte aligned) the staging region of
+  // aa_odd_smem: mbarriers ob_full / ob_free, the plane descriptors, and one
+  // staging row of SLOT elements per plane
+  unsigned char* oreg = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(ring + ST * stage_elems) + 127) & ~uintptr_t(127));
+  uint64_t* ob_full = reinterpret_cast<uint64_t*>(oreg);
+  uint64_t* ob_free = ob_full + 1;
+  AaPlane* infos = reinterpret_cast<AaPlane*>(oreg + 128);
+  T* ostage = reinterpret_cast<T*>(oreg + 128 + (L::Q * 16 + 127) / 128 * 128);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_addr(full + s), 1);
       mbar_init(smem_addr(empty + s), Sh::kConsumerWarps);
+    }
+    if (ODD) {
+      mbar_init(smem_addr(ob_full), Sh::kConsumerWarps);
+      mbar_init(smem_addr(ob_free), Sh::kConsumerWarps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -126,6 +148,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
   TileWalk w(a.ntiles, a.ntx, G.ny);
   int s = 0;
   uint32_t u = 0;
+  int kt = 0;  // tiles done by this block
   for (; w.more(); w.next()) {
     if (!mbar_wait_warp(smem_addr(full + s), u & 1u, abort_flag, a.err, a.timeout_ns)) break;
     const int y = w.y, z = w.z;
@@ -198,37 +221,16 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
     const unsigned bad = collide_v<L, COLL, FORCE, V>(g, a.c);
     bool anybad = act[0] && (bad & 1u);
     if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
-    // odd step: destination row deltas (elements) for e_y = +1 / -1 and
-    // e_z = +1 / -1, with the periodic wrap folded in; kWall marks a wall
-    constexpr long long kWall = -(1LL << 62);
-    const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
-    long long yp = 0, ym = 0, zp = 0, zm = 0;
-    bool xedge = false;  // this thread holds a row end (x wrap or x wall)
-    if constexpr (ODD) {
-      yp = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kWall);
-      ym = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kWall);
-      if (L::D == 3) {
-        zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
-        zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
-      }
-      // only a thread that owns the row's first or last node needs the
-      // per-node wrap / wall test
-#pragma unroll
-      for (int n = 0; n < NPT; ++n) {
-        const int x = x0 + jn[n];
-        xedge |= act[n] && (x == 0 || x == G.nx - 1);
-      }
-    }
     R out[NPT];
+    if constexpr (!ODD) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      if constexpr (PACK) {
-        out[0] = g[i].x;
-        out[NPT - 1] = g[i].y;
-      } else {
-        out[0] = g[i];
-      }
-      if constexpr (!ODD) {
+      for (int i = 0; i < L::Q; ++i) {
+        if constexpr (PACK) {
+          out[0] = g[i].x;
+          out[NPT - 1] = g[i].y;
+        } else {
+          out[0] = g[i];
+        }
         // even: f*_i(x) into the opposite slot of the node's own row
         T* op = buf + L::opp(i) * G.plane + own + x0;
         if constexpr (ADJ) {
@@ -239,48 +241,131 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
           for (int n = 0; n < NPT; ++n)
             if (act[n]) op[jn[n]] = S::enc(out[n]);
         }
-      } else {
-        // odd: f*_i(x) into slot (i, x + e_i), or (ibar, x) beyond a wall
+      }
+    } else {
+      // odd: f*_i(x) goes to slot (i, x + e_i), or to (ibar, x) where x + e_i is
+      // beyond a wall.  Destination row deltas (elements) for e_y = +1 / -1 and
+      // e_z = +1 / -1 with the periodic wrap folded in; kWall marks a wall.
+      constexpr long long kWall = -(1LL << 62);
+      const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
+      const long long yp = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kWall);
+      const long long ym = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kWall);
+      long long zp = 0, zm = 0;
+      if (L::D == 3) {
+        zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
+        zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
+      }
+      // (1) the staging rows are free once every consumer warp has copied the
+      // previous tile's rows out
+      if (kt > 0 && !mbar_wait_warp(smem_addr(ob_free), (uint32_t)((kt - 1) & 1), abort_flag, a.err,
+                                    a.timeout_ns))
+        break;
+      // (2) destination of every plane (threads ct < Q) and the staged values:
+      // staging row i holds destination x at element HT + (x - x0), so each
+      // node's value lands at HT + j + sh_i with sh_i = e_ix (0 beyond a wall)
+      if (ct < L::Q) {
+        int ex = 0, ey = 0, ez = 0;
+#pragma unroll
+        for (int kk = 0; kk < L::Q; ++kk)
+          if (kk == ct) {
+            ex = L::cx(kk);
+            ey = L::cy(kk);
+            ez = L::cz(kk);
+          }
+        const long long dy = ey == 1 ? yp : (ey == -1 ? ym : 0);
+        const long long dz = ez == 1 ? zp : (ez == -1 ? zm : 0);
+        const bool rw = dy == kWall || dz == kWall;
+        const int sh = rw ? 0 : ex;
+        AaPlane pd;
+        pd.off = rw ? (long long)opp_dyn<L>(ct) * G.plane + own : (long long)ct * G.plane + own + dy + dz;
+        pd.lo = max(x0 + sh, x0);
+        pd.hi = min(min(x0 + wdt + sh, G.nx), x0 + XT);
+        infos[ct] = pd;
+      }
+      // a thread that holds the tile's first or last node may have values for
+      // outside the tile's window or the row (wraps, x walls): stored directly
+      bool tend = false;
+#pragma unroll
+      for (int n = 0; n < NPT; ++n) tend |= act[n] && (jn[n] == 0 || jn[n] == wdt - 1);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if constexpr (PACK) {
+          out[0] = g[i].x;
+          out[NPT - 1] = g[i].y;
+        } else {
+          out[0] = g[i];
+        }
         const int ex = L::cx(i);
         const long long dy = L::cy(i) == 1 ? yp : (L::cy(i) == -1 ? ym : 0);
         const long long dz = L::cz(i) == 1 ? zp : (L::cz(i) == -1 ? zm : 0);
-        const bool rwall = dy == kWall || dz == kWall;
-        T* rowd = buf + i * G.plane + own + (rwall ? 0 : dy + dz);
-        T* rowo = buf + L::opp(i) * G.plane + own;
-        bool done = false;
+        const bool rw = dy == kWall || dz == kWall;
+        T* orow = ostage + i * SLOT + HT;
+        bool staged = false;
         if constexpr (ADJ) {
-          if (ex == 0 && !rwall) {
-            if (act[NPT - 1])
-              *reinterpret_cast<uint32_t*>(rowd + x0 + jn[0]) = S::enc2(out[0], out[NPT - 1]);
-            else if (act[0])
-              rowd[x0 + jn[0]] = S::enc(out[0]);
-            done = true;
+          if (ex == 0) {  // the pair's word, 4-byte aligned (HT and jn[0] even)
+            if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(orow + jn[0]) = S::enc2(out[0], out[NPT - 1]);
+            else if (act[0]) orow[jn[0]] = S::enc(out[0]);
+            staged = true;
           }
         }
-        if (!done) {
-          if (!xedge && !rwall) {
-            // away from the row ends: a fixed shift
+        if (!staged) {
+          const int sh = rw ? 0 : ex;
 #pragma unroll
-            for (int n = 0; n < NPT; ++n)
-              if (act[n]) rowd[x0 + jn[n] + ex] = S::enc(out[n]);
-          } else {
+          for (int n = 0; n < NPT; ++n)
+            if (act[n]) orow[jn[n] + sh] = S::enc(out[n]);
+        }
+        if (ex != 0) {
+          if (tend && !rw) {
 #pragma unroll
             for (int n = 0; n < NPT; ++n) {
-              if (!act[n]) continue;
               const int x = x0 + jn[n];
-              int xd = x + ex;
-              bool wl = rwall;
-              if (xd < 0 || xd >= G.nx) {
-                if (G.per[0]) xd = xd < 0 ? xd + G.nx : xd - G.nx;
-                else wl = true;
+              const int xd = x + ex;
+              if (!act[n] || (xd >= x0 && xd < min(x0 + XT, G.nx))) continue;
+              if (xd >= 0 && xd < G.nx) {
+                buf[i * G.plane + own + dy + dz + xd] = S::enc(out[n]);  // next / previous tile's window
+              } else if (G.per[0]) {
+                buf[i * G.plane + own + dy + dz + (xd < 0 ? xd + G.nx : xd - G.nx)] = S::enc(out[n]);
+              } else {
+                buf[L::opp(i) * G.plane + own + x] = S::enc(out[n]);  // x wall: own opposite slot
               }
-              if (wl) rowo[x] = S::enc(out[n]);
-              else rowd[xd] = S::enc(out[n]);
             }
           }
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(ob_full));
+      if (!mbar_wait_warp(smem_addr(ob_full), (uint32_t)(kt & 1), abort_flag, a.err, a.timeout_ns))
+        break;
+      // (3) every staging row to its destination row as aligned 16-byte chunks:
+      // thread ct copies chunk kc of planes sub, sub + PPR, ...  Only elements in
+      // [lo, hi) are written (the tile's own destinations); a chunk that is not
+      // wholly inside goes element by element.
+      {
+        constexpr int VE = 16 / (int)sizeof(T);
+        constexpr int CP = XT / VE;                   // chunks per plane
+        constexpr int PPR = Sh::kConsumers / CP;      // planes per round
+        static_assert(XT % VE == 0 && Sh::kConsumers % CP == 0 && PPR >= 1, "chunk split");
+        const int sub = ct / CP, kc = ct % CP;
+        const int cx0 = x0 + kc * VE;
+#pragma unroll
+        for (int r = 0; r < (L::Q + PPR - 1) / PPR; ++r) {
+          const int i = r * PPR + sub;
+          if (i >= L::Q) continue;
+          const AaPlane pd = infos[i];
+          const T* orow = ostage + i * SLOT + HT + kc * VE;
+          T* drow = buf + pd.off;
+          if (cx0 >= pd.lo && cx0 + VE <= pd.hi) {
+            *reinterpret_cast<uint4*>(drow + cx0) = *reinterpret_cast<const uint4*>(orow);
+          } else {
+            const int e0 = max(cx0, pd.lo), e1 = min(cx0 + VE, pd.hi);
+            for (int e = e0; e < e1; ++e) drow[e] = orow[e - cx0];
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(ob_free));
     }
+    ++kt;
     record_bad(a.flag, a.step, anybad);
   }
 }

@@ -133,8 +133,18 @@ std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked) {
     static const int depths[] = {4, 3, 6, 8, 2};
     for (int X : tiles)
       for (int st : depths) {
-        const size_t smem = ops->tma_smem(X, st);
-        if (smem > 0 && smem <= 200 * 1024) v.push_back(Variant{1, 0, 0, 0, X, st});
+        size_t smem = ops->tma_smem(X, st);
+        // the AA odd step stages its destination rows as well
+        if (smem > 0 && pl.p.layout == LBM_LAYOUT_AA) smem += aa_odd_smem(pl.Q, pl.esize, X);
+        if (smem > 0 && smem <= 200 * 1024) {
+          v.push_back(Variant{1, 0, 0, 0, X, st});
+          v.push_back(Variant{1, 0, 2, 0, X, st});  // at most two resident blocks per SM
+        }
+        // A/B with 32- or 16-bit storage: the staged bulk stores (a store warp)
+        const size_t bs = ops->tma_smem(X, st) + tma_bs_smem(pl.Q, pl.esize, X);
+        if (pl.p.layout == LBM_LAYOUT_AB && pl.esize < 8 && ops->tma_smem(X, st) > 0 &&
+            bs <= 200 * 1024)
+          v.push_back(Variant{1, 0, 0, 1, X, st});
       }
   }
   for (int k = 0; k < ops->n_nv; ++k) {
@@ -652,7 +662,11 @@ int lbm_variant_count(const lbm_ctx* c, int* n) {
 int lbm_variant_name(const lbm_ctx* c, int v, char* buf, size_t len) {
   if (!c || !buf || v < 0 || v >= (int)c->vars.size()) return fail(LBM_ERR_ARG, "bad variant");
   const Variant& x = c->vars[v];
-  if (x.kind == 1)
+  if (x.kind == 1 && x.by == 1)
+    snprintf(buf, len, "tma_X%d_s%d_bs", x.X, x.stages);
+  else if (x.kind == 1 && x.bx > 0)
+    snprintf(buf, len, "tma_X%d_s%d_b%d", x.X, x.stages, x.bx);
+  else if (x.kind == 1)
     snprintf(buf, len, "tma_X%d_s%d", x.X, x.stages);
   else
     snprintf(buf, len, "nv%d_b%dx%d", x.nv, x.bx, x.by);

@@ -18,8 +18,9 @@ struct GeoH {
 struct Variant {
   int kind;    // 0: register kernel (one warp row per block row), 1: bulk-copy pipelined kernel
   int nv;      // kind 0: nodes per thread along x
-  int bx;      // kind 0: threads per block along x (multiple of 32)
-  int by;      // kind 0: rows per block
+  int bx;      // kind 0: threads per block along x (multiple of 32); kind 1: at most this
+               // many resident blocks per SM (0: as many as fit)
+  int by;      // kind 0: rows per block; kind 1: 1 for the staged bulk stores (A/B)
   int X;       // kind 1: tile width (nodes)
   int stages;  // kind 1: shared-memory ring depth
 };
@@ -133,6 +134,24 @@ struct Ops {
   // shared-memory bytes of the pipelined kernel for a tile width and ring depth (0: unsupported)
   size_t (*tma_smem)(int X, int stages);
 };
+
+// Shared memory the odd step of the pipelined AA kernel needs beyond its ring:
+// two mbarriers (padded to 128 bytes), the per-plane destination descriptors
+// (16 bytes each) and one staging row per plane of X + 2 * (16 / esize)
+// elements, each part rounded to 128 bytes; plus 128 bytes of alignment slack
+// for where the ring ends.
+inline constexpr size_t aa_odd_smem(int Q, int esize, int X) {
+  return 128 + 128 + ((size_t)Q * 16 + 127) / 128 * 128 +
+         ((size_t)Q * (size_t)(X + 2 * (16 / esize)) * (size_t)esize + 127) / 128 * 128;
+}
+
+// Shared memory the staged bulk stores of the pipelined A/B kernel (MODE 3)
+// need beyond its ring: 128 bytes of alignment slack, four mbarriers (padded to
+// 128 bytes) and two staging buffers of Q rows of X elements, each rounded to
+// 128 bytes.
+inline constexpr size_t tma_bs_smem(int Q, int esize, int X) {
+  return 128 + 128 + 2 * (((size_t)Q * (size_t)X * (size_t)esize + 127) / 128 * 128);
+}
 
 // Per-direction collision constants from the rates and the force (host, FP64).
 template <class L>

@@ -41,6 +41,7 @@
 #include <type_traits>
 
 #include "collide_v.cuh"
+#include "dispatch.h"
 #include "kernels.cuh"
 #include "storage.cuh"
 
@@ -49,12 +50,14 @@ namespace lbm {
 // One producer warp plus X / NPT consumer threads (NPT = 2 nodes per thread with
 // the packed arithmetic, 1 otherwise): every consumer thread owns one node pair
 // (x0 + j, x0 + j + X/2) -- or one node -- of each tile.
-template <int X, bool PACK>
+// SW = 1 adds a store warp (warp 1) between the producer and the consumers.
+template <int X, bool PACK, int SW = 0>
 struct TmaShape {
   static constexpr int kNPT = PACK ? 2 : 1;
   static constexpr int kConsumers = X / kNPT;
   static constexpr int kConsumerWarps = kConsumers / 32;
-  static constexpr int kThreads = 32 + kConsumers;
+  static constexpr int kBase = 32 * (1 + SW);  // first consumer thread
+  static constexpr int kThreads = kBase + kConsumers;
   static_assert(kConsumers % 32 == 0, "tile width must give whole consumer warps");
 };
 
@@ -111,6 +114,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+// shared -> global bulk copy (both addresses 16-byte aligned, bytes a multiple
+// of 16), tracked by the issuing thread's bulk-async groups
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the sources of every committed group have been read (the shared memory may be reused)
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// every committed group has completed
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// orders this thread's shared-memory writes before later bulk copies that read them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ long long tma_now() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -291,19 +313,22 @@ __device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R
 // GB300: +6% (D3Q19 FP16) and +11% (D2Q9 FP32) over no hint.
 // D3Q27 FP32 asks for 3: at two blocks its 160-thread blocks leave the SM
 // short of consumer warps (occupancy, not registers, limits it).
-template <class L, class S>
+// With the staged bulk stores (MODE 3, one more warp) 16-bit storage asks for
+// 3: at 4 blocks of 256 threads the 64-register cap spills.
+template <class L, class S, int MODE = 0>
 constexpr int tma_min_blocks() {
   if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : 3;
+  if (MODE == 3 && sizeof(typename S::T) == 2) return 3;
   return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
 }
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, int MODE = 0>
-__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L, S>())
+__global__ void __launch_bounds__(TmaShape<XT, PACK, MODE == 3 ? 1 : 0>::kThreads, tma_min_blocks<L, S, MODE>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
   using V = typename std::conditional<PACK, F2, R>::type;
-  using Sh = TmaShape<XT, PACK>;
+  using Sh = TmaShape<XT, PACK, MODE == 3 ? 1 : 0>;
   constexpr int HT = 16 / (int)sizeof(T);  // halo (elements)
   constexpr int SLOT = XT + 2 * HT;        // elements per plane slot
   extern __shared__ __align__(128) unsigned char smem[];
@@ -316,11 +341,26 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
   using Ph = TmaPhi<L, R, XT>;
   constexpr long long pop_bytes = (long long)L::Q * SLOT * sizeof(T);
   constexpr long long stage_bytes = pop_bytes + (MODE == 2 ? Ph::kBytes : 0);
+  // MODE 3: after the ring (128-byte aligned) the staging region of
+  // tma_bs_smem: ob_full[2], ob_free[2], then staging buffers 0 and 1 of Q
+  // rows of XT elements (row i holds plane i of the tile's nodes)
+  constexpr long long kOutElems = ((long long)L::Q * XT * sizeof(T) + 127) / 128 * 128 / sizeof(T);
+  unsigned char* oreg = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(ringb + ST * stage_bytes) + 127) & ~uintptr_t(127));
+  uint64_t* ob_full = reinterpret_cast<uint64_t*>(oreg);
+  uint64_t* ob_free = ob_full + 2;
+  T* outs = reinterpret_cast<T*>(oreg + 128);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_addr(full + s), 1);
       mbar_init(smem_addr(empty + s), Sh::kConsumerWarps);
+    }
+    if (MODE == 3) {
+      for (int b = 0; b < 2; ++b) {
+        mbar_init(smem_addr(ob_full + b), Sh::kConsumerWarps);
+        mbar_init(smem_addr(ob_free + b), 1);
+      }
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -450,6 +490,38 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
     return;
   }
 
+  if constexpr (MODE == 3) {
+    if (warp == 1) {
+      // ---------------------------------------------------------- store warp
+      // Tile k's post-collision rows wait in staging buffer k & 1; lane i copies
+      // row i to plane i of the tile's row segment with one bulk copy (the
+      // 16-byte multiple; a ragged tile's remaining elements one by one), then
+      // hands the buffer back once its rows have been read.
+      TileWalk w(a.ntiles, a.ntx, G.ny);
+      for (int k = 0; w.more(); w.next(), ++k) {
+        const int b = k & 1;
+        if (!mbar_wait_warp(smem_addr(ob_full + b), (uint32_t)((k >> 1) & 1), abort_flag, a.err,
+                            a.timeout_ns))
+          break;
+        if (lane < L::Q) {
+          const int x0 = w.tx * XT;
+          const int wdt = min(XT, G.nx - x0);
+          const T* so = outs + b * kOutElems + lane * XT;
+          T* gd = dst + (long long)lane * G.plane + ((long long)w.z * G.ny + w.y) * G.pitch + x0;
+          const int nb = (wdt * (int)sizeof(T)) & ~15;
+          if (nb > 0) bulk_s2g(gd, smem_addr(so), (uint32_t)nb);
+          for (int e = nb / (int)sizeof(T); e < wdt; ++e) gd[e] = so[e];
+          bulk_commit();
+          bulk_wait_read0();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(ob_free + b));
+      }
+      if (lane < L::Q) bulk_wait_all0();
+      return;
+    }
+  }
+
   // -------------------------------------------------------------- consumers
   constexpr int NPT = Sh::kNPT;
   // 16-bit storage: a thread's node pair is adjacent (x0 + 2j, x0 + 2j + 1), so
@@ -457,13 +529,14 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
   // 32-bit storage keeps the split pair (x0 + j, x0 + j + X/2), whose scalar
   // shared reads are free of bank conflicts for every x shift.
   constexpr bool ADJ = PACK && sizeof(T) == 2;
-  const int ct = threadIdx.x - 32;  // 0 .. kConsumers-1: this thread's node (pair)
+  const int ct = threadIdx.x - Sh::kBase;  // 0 .. kConsumers-1: this thread's node (pair)
   int jn[NPT];
   jn[0] = ADJ ? 2 * ct : ct;
   if (PACK) jn[NPT - 1] = ADJ ? 2 * ct + 1 : ct + XT / 2;
   TileWalk w(a.ntiles, a.ntx, G.ny);
   int s = 0;
   uint32_t u = 0;
+  int kt = 0;  // MODE 3: tiles done by this block
   for (; w.more(); w.next()) {
     if (!mbar_wait_warp(smem_addr(full + s), u & 1u, abort_flag, a.err, a.timeout_ns)) break;
     const int y = w.y, z = w.z;
@@ -614,7 +687,51 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
     }
     bool anybad = act[0] && (bad & 1u);
     if (PACK) anybad = anybad || (act[NPT - 1] && (bad & 2u));
+    if constexpr (MODE == 3) {
+      // into staging buffer kt & 1 (free once the store warp has read tile kt - 2)
+      const int b = kt & 1;
+      if (kt >= 2 && !mbar_wait_warp(smem_addr(ob_free + b), (uint32_t)(((kt >> 1) - 1) & 1), abort_flag,
+                                     a.err, a.timeout_ns))
+        break;
+      T* ob = outs + b * kOutElems;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        T* orow = ob + i * XT;
+        if constexpr (ADJ) {
+          if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(orow + jn[0]) = S::enc2(g[i].x, g[i].y);
+          else if (act[0]) orow[jn[0]] = S::enc(g[i].x);
+        } else if constexpr (PACK) {
+          if (act[0]) orow[jn[0]] = S::enc(g[i].x);
+          if (act[NPT - 1]) orow[jn[NPT - 1]] = S::enc(g[i].y);
+        } else {
+          if (act[0]) orow[jn[0]] = S::enc(g[i]);
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(ob_full + b));
+      record_bad(a.flag, a.step, anybad);
+      ++kt;
+      continue;
+    }
     T* op = dst + own + x0;
+    if (wdt == XT) {
+      // a full tile: every node is active, the stores need no per-plane test
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if constexpr (ADJ) {
+          *reinterpret_cast<uint32_t*>(op + jn[0]) = S::enc2(g[i].x, g[i].y);
+        } else if constexpr (PACK) {
+          op[jn[0]] = S::enc(g[i].x);
+          op[jn[NPT - 1]] = S::enc(g[i].y);
+        } else {
+          op[jn[0]] = S::enc(g[i]);
+        }
+        op += G.plane;
+      }
+      record_bad(a.flag, a.step, anybad);
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       if constexpr (ADJ) {

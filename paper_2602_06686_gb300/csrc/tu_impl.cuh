@@ -673,21 +673,28 @@ struct TU {
     }
     size_t smem = tma_smem(XT, a.stages);
     if (MODE == 2 && smem > 0) smem += (size_t)a.stages * TmaPhi<L, R, XT>::kBytes;
+    // 0: A/B, 1: AA even step, 2: AA odd step, 3: A/B with the staged bulk
+    // stores (MODE 0 only, packed arithmetic); MODE 1 / 2: A/B only
+    int kind = MODE != 0 ? 0 : (s.layout == 1 ? 1 + (s.parity & 1) : 0);
+    if (kind == 0 && MODE == 0 && kPack && s.v.by == 1) kind = 3;
+    if (kind == 2 && smem > 0) smem += aa_odd_smem(L::Q, (int)sizeof(T), XT);
+    if (kind == 3 && smem > 0) smem += tma_bs_smem(L::Q, (int)sizeof(T), XT);
     if (smem == 0 || smem > 227 * 1024 || a.stages > 8) return cudaErrorInvalidValue;
-    // 0: A/B, 1: AA even step, 2: AA odd step (MODE 0); MODE 1 / 2: A/B only
-    const int kind = MODE != 0 ? 0 : (s.layout == 1 ? 1 + (s.parity & 1) : 0);
     void (*kern)(TmaArgs<R>);
+    int threads = Sh::kThreads;
     if constexpr (MODE != 0) {
       kern = &k_step_tma<L, COLL, S, FORCE, kPack, XT, MODE>;
     } else {
       kern = kind == 0   ? &k_step_tma<L, COLL, S, FORCE, kPack, XT>
              : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
-                         : &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>;
+             : kind == 2 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>
+                         : &k_step_tma<L, COLL, S, FORCE, kPack, XT, kPack ? 3 : 0>;
+      if (kind == 3) threads = TmaShape<XT, kPack, 1>::kThreads;
     }
     // per instantiation and kind: the shared-memory opt-in (once) and the
     // resident blocks per SM for each ring depth (cached)
-    static bool attr_set[3] = {false, false, false};
-    static int per_sm_cache[3][9] = {};
+    static bool attr_set[4] = {false, false, false, false};
+    static int per_sm_cache[4][9] = {};
     if (!attr_set[kind]) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       if (e != cudaSuccess) return e;
@@ -695,14 +702,15 @@ struct TU {
     }
     int per_sm = per_sm_cache[kind][a.stages];
     if (per_sm == 0) {
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem);
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
       if (e != cudaSuccess) return e;
       if (per_sm < 1) return cudaErrorInvalidConfiguration;
       per_sm_cache[kind][a.stages] = per_sm;
     }
-    long long blocks = (long long)per_sm * (s.sms > 0 ? s.sms : 1);
+    const int resident = s.v.bx > 0 && s.v.bx < per_sm ? s.v.bx : per_sm;
+    long long blocks = (long long)resident * (s.sms > 0 ? s.sms : 1);
     if (blocks > a.ntiles) blocks = a.ntiles;
-    kern<<<(unsigned)blocks, Sh::kThreads, smem, s.stream>>>(a);
+    kern<<<(unsigned)blocks, threads, smem, s.stream>>>(a);
     return cudaGetLastError();
   }
 

@@ -5,7 +5,10 @@ pitch) and inside its shared-memory slot.  The copy lists are re-derived here
 from the producers' rules (tile windows with a 16-byte halo, wrap copies at
 periodic row ends, the Scheme II Phi rows, the batched kernel's side slots for
 unaligned periodic rows) and checked over many extents, tile widths and
-periodicities.  Nothing here runs on a GPU."""
+periodicities.  The stores staged in shared memory are checked the same way:
+the store warp's shared-to-global bulk copies, and the in-place odd step's
+aligned chunks, which together with its single elements must write every
+destination slot exactly once.  Nothing here runs on a GPU."""
 import itertools
 
 import numpy as np
@@ -109,3 +112,84 @@ def test_batched_windows_and_side_slots(esize):
                     if xe == nx:
                         side.append((0, H, H))
                     _check(side, esize, pitch, 2 * H)
+
+
+@pytest.mark.parametrize("esize,widths", [(4, (256, 384, 512)), (2, (256, 384, 512))])
+def test_staged_bulk_store_rows(esize, widths):
+    """MODE 3 of k_step_tma: the store warp copies each staging row (plane i of
+    the tile) to [x0, x0 + wdt) of its destination row: one bulk copy of the
+    16-byte multiple of the row segment (16-byte aligned in global and shared
+    memory), then the remaining elements one by one; together they write the
+    segment exactly once, inside the row and inside the staging row."""
+    H = 16 // esize
+    rng = np.random.default_rng(5)
+    for nx in sorted({2 * H, 3 * H} | {int(v) * H for v in rng.integers(2, 400, 60)}):
+        pitch = _pitch(nx, esize)
+        for X in widths:
+            for x0 in range(0, nx, X):
+                wdt = min(X, nx - x0)
+                nb = (wdt * esize) // 16 * 16 // esize
+                if nb:
+                    _check([(x0, nb, 0)], esize, pitch, X)
+                written = list(range(x0, x0 + nb)) + list(range(x0 + nb, x0 + wdt))
+                assert written == list(range(x0, x0 + wdt))
+                assert x0 + wdt <= nx <= pitch
+
+
+def _aa_odd_writes(nx, X, esize, per, ex, rw):
+    """Destinations written for one plane of one row by the staged AA odd step:
+    aligned 16-byte chunks and single elements from the staging row, and the
+    direct stores of the tile-end threads (wraps, x walls as ("opp", x))."""
+    VE = 16 // esize
+    sh = 0 if rw else ex
+    vec, single = [], []
+    for x0 in range(0, nx, X):
+        wdt = min(X, nx - x0)
+        lo, hi = max(x0 + sh, x0), min(x0 + wdt + sh, nx, x0 + X)
+        for kc in range(X // VE):
+            cx0 = x0 + kc * VE
+            if cx0 >= lo and cx0 + VE <= hi:
+                vec.append(cx0)
+            else:
+                single += list(range(max(cx0, lo), min(cx0 + VE, hi)))
+        if ex != 0 and not rw:
+            for j in {0, wdt - 1}:
+                x = x0 + j
+                xd = x + ex
+                if x0 <= xd < min(x0 + X, nx):
+                    continue
+                if 0 <= xd < nx:
+                    single.append(xd)
+                elif per:
+                    single.append(xd % nx)
+                else:
+                    single.append(("opp", x))
+    return vec, single
+
+
+@pytest.mark.parametrize("esize,widths", [(4, (256, 384, 512)), (2, (256, 384, 512)),
+                                          (8, (128, 192, 256))])
+def test_aa_odd_staged_stores_cover_each_slot_once(esize, widths):
+    """k_step_aa_tma, odd step: node x writes f*_i to x + e_ix of the
+    destination row (wrapped across a periodic x axis, bounced to its own
+    opposite slot at an x wall; a plane whose destination row lies beyond a y /
+    z wall goes to the node's own row unshifted).  The staged copy (aligned
+    16-byte chunks inside the tile's window [lo, hi), single elements at its
+    ends) and the tile-end threads' direct stores must write every destination
+    exactly once, with every chunk 16-byte aligned and inside the row."""
+    VE = 16 // esize
+    rng = np.random.default_rng(6)
+    for nx in sorted({2 * VE, 3 * VE} | {int(v) * VE for v in rng.integers(2, 300, 40)}):
+        pitch = _pitch(nx, esize)
+        for X, per, ex, rw in itertools.product(widths, (0, 1), (-1, 0, 1), (False, True)):
+            vec, single = _aa_odd_writes(nx, X, esize, per, ex, rw)
+            for c in vec:
+                _check([(c, VE, 0)], esize, pitch, VE)
+            written = [x for c in vec for x in range(c, c + VE)] + single
+            sh = 0 if rw else ex
+            want = []
+            for x in range(nx):
+                xd = x + sh
+                want.append(xd if 0 <= xd < nx else (xd % nx if per else ("opp", x)))
+            key = lambda v: (1, v[1]) if isinstance(v, tuple) else (0, v)
+            assert sorted(written, key=key) == sorted(want, key=key), (nx, X, per, ex, rw)
