@@ -24,21 +24,35 @@
 
 namespace lbm {
 
-// Destination of one plane's staged row in the odd step: element offset of
-// the destination row (plane and row), and the window [lo, hi) of x that this
-// tile's nodes write there.
-struct alignas(16) AaPlane {
-  long long off;
-  int lo, hi;
-};
+// Destination row of plane i for the odd step at tile row (y, z): the row
+// offset (elements) of plane i shifted by e_iy, e_iz with the periodic wrap,
+// or kAaWall when that row lies beyond a non-periodic wall.
+constexpr long long kAaWall = -(1LL << 62);
+__device__ __forceinline__ long long aa_row_delta(const Geo& G, int y, int z, int ey, int ez) {
+  const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
+  long long d = 0;
+  if (ey == 1) d = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kAaWall);
+  if (ey == -1) d = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kAaWall);
+  if (d == kAaWall) return d;
+  if (ez == 1) {
+    const long long e = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kAaWall);
+    return e == kAaWall ? e : d + e;
+  }
+  if (ez == -1) {
+    const long long e = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kAaWall);
+    return e == kAaWall ? e : d + e;
+  }
+  return d;
+}
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, bool ODD>
-__global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L, S>())
+__global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
+                                  tma_min_blocks<L, S, ODD ? 3 : 0>())
     k_step_aa_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
   using V = typename std::conditional<PACK, F2, R>::type;
-  using Sh = TmaShape<XT, PACK>;
+  using Sh = TmaShape<XT, PACK, ODD ? 1 : 0>;
   constexpr int HT = 16 / (int)sizeof(T);
   constexpr int SLOT = XT + 2 * HT;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -50,14 +64,13 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
   T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
   constexpr long long stage_elems = (long long)L::Q * SLOT;
   // odd step: after the ring (128-byte aligned) the staging region of
-  // aa_odd_smem: mbarriers ob_full / ob_free, the plane descriptors, and one
-  // staging row of SLOT elements per plane
+  // aa_odd_smem: mbarriers ob_full / ob_free, then one staging row of SLOT
+  // elements per plane
   unsigned char* oreg = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(ring + ST * stage_elems) + 127) & ~uintptr_t(127));
   uint64_t* ob_full = reinterpret_cast<uint64_t*>(oreg);
   uint64_t* ob_free = ob_full + 1;
-  AaPlane* infos = reinterpret_cast<AaPlane*>(oreg + 128);
-  T* ostage = reinterpret_cast<T*>(oreg + 128 + (L::Q * 16 + 127) / 128 * 128);
+  T* ostage = reinterpret_cast<T*>(oreg + 128);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -66,7 +79,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
     }
     if (ODD) {
       mbar_init(smem_addr(ob_full), Sh::kConsumerWarps);
-      mbar_init(smem_addr(ob_free), Sh::kConsumerWarps);
+      mbar_init(smem_addr(ob_free), 1);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -138,10 +151,56 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
     return;
   }
 
+  if constexpr (ODD) {
+    if (warp == 1) {
+      // ---------------------------------------------------------- store warp
+      // The staging rows of tile k hold the destinations [lo, hi) of every
+      // plane (row i: destination x at element HT + x - x0).  Lane i writes
+      // plane i: the 16-byte aligned interior by one bulk copy, the few
+      // elements at either end one by one; then the rows are handed back.
+      constexpr int VE = 16 / (int)sizeof(T);
+      TileWalk w(a.ntiles, a.ntx, G.ny);
+      for (int k = 0; w.more(); w.next(), ++k) {
+        if (!mbar_wait_warp(smem_addr(ob_full), (uint32_t)(k & 1), abort_flag, a.err, a.timeout_ns)) break;
+        if (lane < L::Q) {
+          const int y = w.y, z = w.z;
+          const int x0 = w.tx * XT;
+          const int wdt = min(XT, G.nx - x0);
+          const long long own = ((long long)z * G.ny + y) * G.pitch;
+          int ex = 0, ey = 0, ez = 0;
+#pragma unroll
+          for (int kk = 0; kk < L::Q; ++kk)
+            if (kk == lane) {
+              ex = L::cx(kk);
+              ey = L::cy(kk);
+              ez = L::cz(kk);
+            }
+          const long long dr = aa_row_delta(G, y, z, ey, ez);
+          const bool rw = dr == kAaWall;
+          const int sh = rw ? 0 : ex;
+          T* drow = buf + (rw ? (long long)opp_dyn<L>(lane) * G.plane + own
+                              : (long long)lane * G.plane + own + dr);
+          const T* orow = ostage + lane * SLOT + HT - x0;  // orow[x]: destination x
+          const int lo = max(x0 + sh, x0), hi = min(min(x0 + wdt + sh, G.nx), x0 + XT);
+          const int ca = min(hi, (lo + VE - 1) / VE * VE), cb = max(ca, hi / VE * VE);
+          if (cb > ca) bulk_s2g(drow + ca, smem_addr(orow + ca), (uint32_t)((cb - ca) * sizeof(T)));
+          for (int e = lo; e < ca; ++e) drow[e] = orow[e];
+          for (int e = cb; e < hi; ++e) drow[e] = orow[e];
+          bulk_commit();
+          bulk_wait_read0();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(ob_free));
+      }
+      if (lane < L::Q) bulk_wait_all0();
+      return;
+    }
+  }
+
   // -------------------------------------------------------------- consumers
   constexpr int NPT = Sh::kNPT;
   constexpr bool ADJ = PACK && sizeof(T) == 2;
-  const int ct = threadIdx.x - 32;
+  const int ct = threadIdx.x - Sh::kBase;
   int jn[NPT];
   jn[0] = ADJ ? 2 * ct : ct;
   if (PACK) jn[NPT - 1] = ADJ ? 2 * ct + 1 : ct + XT / 2;
@@ -246,7 +305,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
       // odd: f*_i(x) goes to slot (i, x + e_i), or to (ibar, x) where x + e_i is
       // beyond a wall.  Destination row deltas (elements) for e_y = +1 / -1 and
       // e_z = +1 / -1 with the periodic wrap folded in; kWall marks a wall.
-      constexpr long long kWall = -(1LL << 62);
+      constexpr long long kWall = kAaWall;
       const long long pitch = G.pitch, zstride = (long long)G.ny * G.pitch;
       const long long yp = y + 1 < G.ny ? pitch : (G.per[1] ? -(long long)(G.ny - 1) * pitch : kWall);
       const long long ym = y > 0 ? -pitch : (G.per[1] ? (long long)(G.ny - 1) * pitch : kWall);
@@ -255,33 +314,14 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
         zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
         zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
       }
-      // (1) the staging rows are free once every consumer warp has copied the
-      // previous tile's rows out
+      // (1) the staging rows are free once the store warp has read the
+      // previous tile's rows
       if (kt > 0 && !mbar_wait_warp(smem_addr(ob_free), (uint32_t)((kt - 1) & 1), abort_flag, a.err,
                                     a.timeout_ns))
         break;
-      // (2) destination of every plane (threads ct < Q) and the staged values:
-      // staging row i holds destination x at element HT + (x - x0), so each
-      // node's value lands at HT + j + sh_i with sh_i = e_ix (0 beyond a wall)
-      if (ct < L::Q) {
-        int ex = 0, ey = 0, ez = 0;
-#pragma unroll
-        for (int kk = 0; kk < L::Q; ++kk)
-          if (kk == ct) {
-            ex = L::cx(kk);
-            ey = L::cy(kk);
-            ez = L::cz(kk);
-          }
-        const long long dy = ey == 1 ? yp : (ey == -1 ? ym : 0);
-        const long long dz = ez == 1 ? zp : (ez == -1 ? zm : 0);
-        const bool rw = dy == kWall || dz == kWall;
-        const int sh = rw ? 0 : ex;
-        AaPlane pd;
-        pd.off = rw ? (long long)opp_dyn<L>(ct) * G.plane + own : (long long)ct * G.plane + own + dy + dz;
-        pd.lo = max(x0 + sh, x0);
-        pd.hi = min(min(x0 + wdt + sh, G.nx), x0 + XT);
-        infos[ct] = pd;
-      }
+      // (2) the staged values: staging row i holds destination x at element
+      // HT + (x - x0), so each node's value lands at HT + j + sh_i with
+      // sh_i = e_ix (0 beyond a wall)
       // a thread that holds the tile's first or last node may have values for
       // outside the tile's window or the row (wraps, x walls): stored directly
       bool tend = false;
@@ -332,38 +372,11 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK>::kThreads, tma_min_blocks<L
           }
         }
       }
+      // (3) hand the rows to the store warp (its bulk copies read them through
+      // the async proxy)
+      fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(ob_full));
-      if (!mbar_wait_warp(smem_addr(ob_full), (uint32_t)(kt & 1), abort_flag, a.err, a.timeout_ns))
-        break;
-      // (3) every staging row to its destination row as aligned 16-byte chunks:
-      // thread ct copies chunk kc of planes sub, sub + PPR, ...  Only elements in
-      // [lo, hi) are written (the tile's own destinations); a chunk that is not
-      // wholly inside goes element by element.
-      {
-        constexpr int VE = 16 / (int)sizeof(T);
-        constexpr int CP = XT / VE;                   // chunks per plane
-        constexpr int PPR = Sh::kConsumers / CP;      // planes per round
-        static_assert(XT % VE == 0 && Sh::kConsumers % CP == 0 && PPR >= 1, "chunk split");
-        const int sub = ct / CP, kc = ct % CP;
-        const int cx0 = x0 + kc * VE;
-#pragma unroll
-        for (int r = 0; r < (L::Q + PPR - 1) / PPR; ++r) {
-          const int i = r * PPR + sub;
-          if (i >= L::Q) continue;
-          const AaPlane pd = infos[i];
-          const T* orow = ostage + i * SLOT + HT + kc * VE;
-          T* drow = buf + pd.off;
-          if (cx0 >= pd.lo && cx0 + VE <= pd.hi) {
-            *reinterpret_cast<uint4*>(drow + cx0) = *reinterpret_cast<const uint4*>(orow);
-          } else {
-            const int e0 = max(cx0, pd.lo), e1 = min(cx0 + VE, pd.hi);
-            for (int e = e0; e < e1; ++e) drow[e] = orow[e - cx0];
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_addr(ob_free));
     }
     ++kt;
     record_bad(a.flag, a.step, anybad);

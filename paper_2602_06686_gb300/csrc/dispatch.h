@@ -136,13 +136,11 @@ struct Ops {
 };
 
 // Shared memory the odd step of the pipelined AA kernel needs beyond its ring:
-// two mbarriers (padded to 128 bytes), the per-plane destination descriptors
-// (16 bytes each) and one staging row per plane of X + 2 * (16 / esize)
-// elements, each part rounded to 128 bytes; plus 128 bytes of alignment slack
-// for where the ring ends.
+// two mbarriers (padded to 128 bytes) and one staging row per plane of
+// X + 2 * (16 / esize) elements, rounded to 128 bytes; plus 128 bytes of
+// alignment slack for where the ring ends.
 inline constexpr size_t aa_odd_smem(int Q, int esize, int X) {
-  return 128 + 128 + ((size_t)Q * 16 + 127) / 128 * 128 +
-         ((size_t)Q * (size_t)(X + 2 * (16 / esize)) * (size_t)esize + 127) / 128 * 128;
+  return 128 + 128 + ((size_t)Q * (size_t)(X + 2 * (16 / esize)) * (size_t)esize + 127) / 128 * 128;
 }
 
 // Shared memory the staged bulk stores of the pipelined A/B kernel (MODE 3)

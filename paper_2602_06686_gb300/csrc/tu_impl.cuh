@@ -689,7 +689,7 @@ struct TU {
              : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
              : kind == 2 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>
                          : &k_step_tma<L, COLL, S, FORCE, kPack, XT, kPack ? 3 : 0>;
-      if (kind == 3) threads = TmaShape<XT, kPack, 1>::kThreads;
+      if (kind == 2 || kind == 3) threads = TmaShape<XT, kPack, 1>::kThreads;
     }
     // per instantiation and kind: the shared-memory opt-in (once) and the
     // resident blocks per SM for each ring depth (cached)

@@ -138,20 +138,22 @@ def test_staged_bulk_store_rows(esize, widths):
 
 def _aa_odd_writes(nx, X, esize, per, ex, rw):
     """Destinations written for one plane of one row by the staged AA odd step:
-    aligned 16-byte chunks and single elements from the staging row, and the
-    direct stores of the tile-end threads (wraps, x walls as ("opp", x))."""
+    the store warp's bulk copy of the 16-byte aligned interior of the tile's
+    window [lo, hi) (as (start, elements, staging-row offset)) and its single
+    elements at either end, and the direct stores of the tile-end threads
+    (wraps, x walls as ("opp", x))."""
     VE = 16 // esize
+    HT = VE
     sh = 0 if rw else ex
     vec, single = [], []
     for x0 in range(0, nx, X):
         wdt = min(X, nx - x0)
         lo, hi = max(x0 + sh, x0), min(x0 + wdt + sh, nx, x0 + X)
-        for kc in range(X // VE):
-            cx0 = x0 + kc * VE
-            if cx0 >= lo and cx0 + VE <= hi:
-                vec.append(cx0)
-            else:
-                single += list(range(max(cx0, lo), min(cx0 + VE, hi)))
+        ca = min(hi, (lo + VE - 1) // VE * VE)
+        cb = max(ca, hi // VE * VE)
+        if cb > ca:
+            vec.append((ca, cb - ca, HT + ca - x0))
+        single += list(range(lo, ca)) + list(range(cb, hi))
         if ex != 0 and not rw:
             for j in {0, wdt - 1}:
                 x = x0 + j
@@ -173,19 +175,19 @@ def test_aa_odd_staged_stores_cover_each_slot_once(esize, widths):
     """k_step_aa_tma, odd step: node x writes f*_i to x + e_ix of the
     destination row (wrapped across a periodic x axis, bounced to its own
     opposite slot at an x wall; a plane whose destination row lies beyond a y /
-    z wall goes to the node's own row unshifted).  The staged copy (aligned
-    16-byte chunks inside the tile's window [lo, hi), single elements at its
-    ends) and the tile-end threads' direct stores must write every destination
-    exactly once, with every chunk 16-byte aligned and inside the row."""
+    z wall goes to the node's own row unshifted).  The store warp's copy (the
+    aligned interior of the tile's window [lo, hi) by one bulk copy, single
+    elements at its ends) and the tile-end threads' direct stores must write
+    every destination exactly once; the bulk copy must be 16-byte aligned in
+    the row and in the staging row and stay inside both."""
     VE = 16 // esize
     rng = np.random.default_rng(6)
     for nx in sorted({2 * VE, 3 * VE} | {int(v) * VE for v in rng.integers(2, 300, 40)}):
         pitch = _pitch(nx, esize)
         for X, per, ex, rw in itertools.product(widths, (0, 1), (-1, 0, 1), (False, True)):
             vec, single = _aa_odd_writes(nx, X, esize, per, ex, rw)
-            for c in vec:
-                _check([(c, VE, 0)], esize, pitch, VE)
-            written = [x for c in vec for x in range(c, c + VE)] + single
+            _check(vec, esize, pitch, X + 2 * VE)
+            written = [x for c, n, _ in vec for x in range(c, c + n)] + single
             sh = 0 if rw else ex
             want = []
             for x in range(nx):
