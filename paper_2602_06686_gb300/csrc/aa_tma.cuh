@@ -64,13 +64,15 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
   T* ring = reinterpret_cast<T*>(smem + 128 * ((2 * ST * 8 + 4 + 127) / 128));
   constexpr long long stage_elems = (long long)L::Q * SLOT;
   // odd step: after the ring (128-byte aligned) the staging region of
-  // aa_odd_smem: mbarriers ob_full / ob_free, then one staging row of SLOT
-  // elements per plane
+  // aa_odd_smem: mbarriers ob_full[NB] / ob_free[NB], then NB staging buffers
+  // of one row of SLOT elements per plane (tile k uses buffer k % NB)
+  constexpr int NB = aa_odd_buffers(L::Q);
+  constexpr long long kStageElems = ((long long)L::Q * SLOT * sizeof(T) + 127) / 128 * 128 / sizeof(T);
   unsigned char* oreg = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(ring + ST * stage_elems) + 127) & ~uintptr_t(127));
   uint64_t* ob_full = reinterpret_cast<uint64_t*>(oreg);
-  uint64_t* ob_free = ob_full + 1;
-  T* ostage = reinterpret_cast<T*>(oreg + 128);
+  uint64_t* ob_free = ob_full + NB;
+  T* ostages = reinterpret_cast<T*>(oreg + 128);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -78,8 +80,10 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
       mbar_init(smem_addr(empty + s), Sh::kConsumerWarps);
     }
     if (ODD) {
-      mbar_init(smem_addr(ob_full), Sh::kConsumerWarps);
-      mbar_init(smem_addr(ob_free), 1);
+      for (int b = 0; b < NB; ++b) {
+        mbar_init(smem_addr(ob_full + b), Sh::kConsumerWarps);
+        mbar_init(smem_addr(ob_free + b), 1);
+      }
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -161,7 +165,11 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
       constexpr int VE = 16 / (int)sizeof(T);
       TileWalk w(a.ntiles, a.ntx, G.ny);
       for (int k = 0; w.more(); w.next(), ++k) {
-        if (!mbar_wait_warp(smem_addr(ob_full), (uint32_t)(k & 1), abort_flag, a.err, a.timeout_ns)) break;
+        const int b = k % NB;
+        if (!mbar_wait_warp(smem_addr(ob_full + b), (uint32_t)((k / NB) & 1), abort_flag, a.err,
+                            a.timeout_ns))
+          break;
+        const T* ostage = ostages + b * kStageElems;
         if (lane < L::Q) {
           const int y = w.y, z = w.z;
           const int x0 = w.tx * XT;
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
           bulk_wait_read0();
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(ob_free));
+        if (lane == 0) mbar_arrive(smem_addr(ob_free + b));
       }
       if (lane < L::Q) bulk_wait_all0();
       return;
@@ -314,11 +322,13 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
         zp = z + 1 < G.nz ? zstride : (G.per[2] ? -(long long)(G.nz - 1) * zstride : kWall);
         zm = z > 0 ? -zstride : (G.per[2] ? (long long)(G.nz - 1) * zstride : kWall);
       }
-      // (1) the staging rows are free once the store warp has read the
-      // previous tile's rows
-      if (kt > 0 && !mbar_wait_warp(smem_addr(ob_free), (uint32_t)((kt - 1) & 1), abort_flag, a.err,
-                                    a.timeout_ns))
+      // (1) staging buffer kt % NB is free once the store warp has read the
+      // rows of tile kt - NB
+      const int ob = kt % NB;
+      if (kt >= NB && !mbar_wait_warp(smem_addr(ob_free + ob), (uint32_t)((kt / NB - 1) & 1), abort_flag,
+                                      a.err, a.timeout_ns))
         break;
+      T* ostage = ostages + ob * kStageElems;
       // (2) the staged values: staging row i holds destination x at element
       // HT + (x - x0), so each node's value lands at HT + j + sh_i with
       // sh_i = e_ix (0 beyond a wall)
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
       // the async proxy)
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_addr(ob_full));
+      if (lane == 0) mbar_arrive(smem_addr(ob_full + ob));
     }
     ++kt;
     record_bad(a.flag, a.step, anybad);

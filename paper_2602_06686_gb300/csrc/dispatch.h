@@ -135,12 +135,19 @@ struct Ops {
   size_t (*tma_smem)(int X, int stages);
 };
 
+// Staging buffers of the pipelined AA kernel's odd step: two on D2Q9 (its
+// short collision would otherwise wait for the store warp), one on the 3-D
+// lattices (whose staging rows are large).
+inline constexpr int aa_odd_buffers(int Q) { return Q == 9 ? 2 : 1; }
+
 // Shared memory the odd step of the pipelined AA kernel needs beyond its ring:
-// two mbarriers (padded to 128 bytes) and one staging row per plane of
-// X + 2 * (16 / esize) elements, rounded to 128 bytes; plus 128 bytes of
-// alignment slack for where the ring ends.
+// the mbarriers (padded to 128 bytes) and aa_odd_buffers staging buffers of one
+// row per plane of X + 2 * (16 / esize) elements, each rounded to 128 bytes;
+// plus 128 bytes of alignment slack for where the ring ends.
 inline constexpr size_t aa_odd_smem(int Q, int esize, int X) {
-  return 128 + 128 + ((size_t)Q * (size_t)(X + 2 * (16 / esize)) * (size_t)esize + 127) / 128 * 128;
+  return 128 + 128 +
+         (size_t)aa_odd_buffers(Q) *
+             (((size_t)Q * (size_t)(X + 2 * (16 / esize)) * (size_t)esize + 127) / 128 * 128);
 }
 
 // Shared memory the staged bulk stores of the pipelined A/B kernel (MODE 3)
