@@ -145,6 +145,10 @@ std::vector<Variant> variants_for(const Plan& pl, const Ops* ops, bool masked) {
         if (pl.p.layout == LBM_LAYOUT_AB && pl.esize < 8 && ops->tma_smem(X, st) > 0 &&
             bs <= 200 * 1024)
           v.push_back(Variant{1, 0, 0, 1, X, st});
+        // A/B with 16-bit storage: four nodes per consumer thread
+        if (pl.p.layout == LBM_LAYOUT_AB && pl.esize == 2 && ops->tma_smem(X, st) > 0 &&
+            ops->tma_smem(X, st) <= 200 * 1024)
+          v.push_back(Variant{1, 4, 0, 0, X, st});
       }
   }
   for (int k = 0; k < ops->n_nv; ++k) {
@@ -664,6 +668,8 @@ int lbm_variant_name(const lbm_ctx* c, int v, char* buf, size_t len) {
   const Variant& x = c->vars[v];
   if (x.kind == 1 && x.by == 1)
     snprintf(buf, len, "tma_X%d_s%d_bs", x.X, x.stages);
+  else if (x.kind == 1 && x.nv == 4)
+    snprintf(buf, len, "tma_X%d_s%d_q", x.X, x.stages);
   else if (x.kind == 1 && x.bx > 0)
     snprintf(buf, len, "tma_X%d_s%d_b%d", x.X, x.stages, x.bx);
   else if (x.kind == 1)

@@ -17,7 +17,8 @@ struct GeoH {
 
 struct Variant {
   int kind;    // 0: register kernel (one warp row per block row), 1: bulk-copy pipelined kernel
-  int nv;      // kind 0: nodes per thread along x
+  int nv;      // kind 0: nodes per thread along x; kind 1: 4 for four nodes per consumer
+               // thread (16-bit storage, A/B), else 0
   int bx;      // kind 0: threads per block along x (multiple of 32); kind 1: at most this
                // many resident blocks per SM (0: as many as fit)
   int by;      // kind 0: rows per block; kind 1: 1 for the staged bulk stores (A/B)

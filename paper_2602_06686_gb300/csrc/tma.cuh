@@ -34,7 +34,9 @@
 // the producer also stages the Phi rows a tile's differences need -- Phi_x of
 // the tile's own row with an x halo, Phi_y of rows y-1, y, y+1 and, on D3Q19,
 // Phi_z of rows z-1, z, z+1, wrapped across periodic axes and skipped beyond
-// walls -- so that they arrive with the populations (TmaPhi).
+// walls -- so that they arrive with the populations (TmaPhi).  MODE 3 is the
+// update with the staged bulk stores of a store warp; MODE 4 the update with
+// four adjacent nodes per consumer thread (16-bit storage).
 #pragma once
 #include <stdint.h>
 
@@ -50,10 +52,11 @@ namespace lbm {
 // One producer warp plus X / NPT consumer threads (NPT = 2 nodes per thread with
 // the packed arithmetic, 1 otherwise): every consumer thread owns one node pair
 // (x0 + j, x0 + j + X/2) -- or one node -- of each tile.
-// SW = 1 adds a store warp (warp 1) between the producer and the consumers.
-template <int X, bool PACK, int SW = 0>
+// SW = 1 adds a store warp (warp 1) between the producer and the consumers;
+// NQ = 4 gives every consumer four adjacent nodes (two packed pairs).
+template <int X, bool PACK, int SW = 0, int NQ = 0>
 struct TmaShape {
-  static constexpr int kNPT = PACK ? 2 : 1;
+  static constexpr int kNPT = NQ ? NQ : (PACK ? 2 : 1);
   static constexpr int kConsumers = X / kNPT;
   static constexpr int kConsumerWarps = kConsumers / 32;
   static constexpr int kBase = 32 * (1 + SW);  // first consumer thread
@@ -314,21 +317,24 @@ __device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R
 // D3Q27 FP32 asks for 3: at two blocks its 160-thread blocks leave the SM
 // short of consumer warps (occupancy, not registers, limits it).
 // With the staged bulk stores (MODE 3, one more warp) 16-bit storage asks for
-// 3: at 4 blocks of 256 threads the 64-register cap spills.
+// 3: at 4 blocks of 256 threads the 64-register cap spills.  Four nodes per
+// thread (MODE 4) hold two pairs of populations and ask for 3 as well.
 template <class L, class S, int MODE = 0>
 constexpr int tma_min_blocks() {
   if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : 3;
   if (MODE == 3 && sizeof(typename S::T) == 2) return 3;
+  if (MODE == 4 && sizeof(typename S::T) == 2) return 4;
   return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
 }
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, int MODE = 0>
-__global__ void __launch_bounds__(TmaShape<XT, PACK, MODE == 3 ? 1 : 0>::kThreads, tma_min_blocks<L, S, MODE>())
+__global__ void __launch_bounds__(TmaShape<XT, PACK, MODE == 3 ? 1 : 0, MODE == 4 ? 4 : 0>::kThreads,
+                                  tma_min_blocks<L, S, MODE>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;
   using V = typename std::conditional<PACK, F2, R>::type;
-  using Sh = TmaShape<XT, PACK, MODE == 3 ? 1 : 0>;
+  using Sh = TmaShape<XT, PACK, MODE == 3 ? 1 : 0, MODE == 4 ? 4 : 0>;
   constexpr int HT = 16 / (int)sizeof(T);  // halo (elements)
   constexpr int SLOT = XT + 2 * HT;        // elements per plane slot
   extern __shared__ __align__(128) unsigned char smem[];
@@ -520,6 +526,107 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, MODE == 3 ? 1 : 0>::kThread
       if (lane < L::Q) bulk_wait_all0();
       return;
     }
+  }
+
+  if constexpr (MODE == 4) {
+    // ------------------------------------------- consumers, four nodes each
+    // 16-bit storage: nodes x0 + j0 .. x0 + j0 + 3 (j0 = 4 ct) as two packed
+    // pairs.  Unshifted planes load the four as one 64-bit word, shifted
+    // planes element by element; full tiles store one 64-bit word per plane.
+    static_assert(PACK && sizeof(T) == 2, "four nodes per thread: 16-bit storage");
+    const int j0 = 4 * (threadIdx.x - Sh::kBase);
+    TileWalk w(a.ntiles, a.ntx, G.ny);
+    int s = 0;
+    uint32_t u = 0;
+    for (; w.more(); w.next()) {
+      if (!mbar_wait_warp(smem_addr(full + s), u & 1u, abort_flag, a.err, a.timeout_ns)) break;
+      const int y = w.y, z = w.z;
+      const int x0 = w.tx * XT;
+      const int wdt = min(XT, G.nx - x0);
+      const T* st = reinterpret_cast<const T*>(ringb + s * stage_bytes);
+      const long long own = ((long long)z * G.ny + y) * G.pitch;
+      const bool anywall = (!G.per[1] && (y == 0 || y == G.ny - 1)) ||
+                           (L::D == 3 && !G.per[2] && (z == 0 || z == G.nz - 1));
+      const bool xwall = !G.per[0] && (x0 == 0 || x0 + XT >= G.nx);
+      bool act[4];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) act[n] = j0 + n < wdt;
+      F2 ga[L::Q], gb[L::Q];
+      if (!anywall && !xwall) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const T* slot = st + i * SLOT + HT - L::cx(i);
+          if (L::cx(i) == 0) {
+            // slot + HT is 16-byte aligned and j0 a multiple of 4: one 8-byte word
+            const uint2 wv = *reinterpret_cast<const uint2*>(slot + j0);
+            float a0, a1, a2, a3;
+            S::dec2(wv.x, a0, a1);
+            S::dec2(wv.y, a2, a3);
+            ga[i] = F2{a0, a1};
+            gb[i] = F2{a2, a3};
+          } else {
+            ga[i] = F2{S::dec(slot[j0]), S::dec(slot[j0 + 1])};
+            gb[i] = F2{S::dec(slot[j0 + 2]), S::dec(slot[j0 + 3])};
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const int ex = L::cx(i);
+          const T* slot = st + i * SLOT + HT;
+          int ys, zs;
+          bool wallrow;
+          tma_source_row<L>(G, i, y, z, ys, zs, wallrow);
+          float v[4];
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            const int j = j0 + n;
+            const int x = x0 + j;
+            if (wallrow) {
+              v[n] = S::dec(slot[j]);
+            } else if (!G.per[0] && ((ex == 1 && x == 0) || (ex == -1 && x == G.nx - 1))) {
+              v[n] = act[n] ? S::dec(src[L::opp(i) * G.plane + own + x]) : 0.f;
+            } else {
+              v[n] = S::dec(slot[j - ex]);
+            }
+          }
+          ga[i] = F2{v[0], v[1]};
+          gb[i] = F2{v[2], v[3]};
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(empty + s));
+      if (++s == ST) {
+        s = 0;
+        ++u;
+      }
+      const unsigned ba = collide_v<L, COLL, FORCE, F2>(ga, a.c);
+      const unsigned bb = collide_v<L, COLL, FORCE, F2>(gb, a.c);
+      const bool anybad = (act[0] && (ba & 1u)) || (act[1] && (ba & 2u)) || (act[2] && (bb & 1u)) ||
+                          (act[3] && (bb & 2u));
+      T* op = dst + own + x0 + j0;
+      if (wdt == XT) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          uint2 wv;
+          wv.x = S::enc2(ga[i].x, ga[i].y);
+          wv.y = S::enc2(gb[i].x, gb[i].y);
+          *reinterpret_cast<uint2*>(op) = wv;  // 8-byte aligned: 16-byte rows, j0 a multiple of 4
+          op += G.plane;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const float o[4] = {ga[i].x, ga[i].y, gb[i].x, gb[i].y};
+#pragma unroll
+          for (int n = 0; n < 4; ++n)
+            if (act[n]) op[n] = S::enc(o[n]);
+          op += G.plane;
+        }
+      }
+      record_bad(a.flag, a.step, anybad);
+    }
+    return;
   }
 
   // -------------------------------------------------------------- consumers

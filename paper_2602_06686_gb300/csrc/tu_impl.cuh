@@ -677,6 +677,7 @@ struct TU {
     // stores (MODE 0 only, packed arithmetic); MODE 1 / 2: A/B only
     int kind = MODE != 0 ? 0 : (s.layout == 1 ? 1 + (s.parity & 1) : 0);
     if (kind == 0 && MODE == 0 && kPack && s.v.by == 1) kind = 3;
+    if (kind == 0 && MODE == 0 && kPack && sizeof(T) == 2 && s.v.nv == 4) kind = 4;
     if (kind == 2 && smem > 0) smem += aa_odd_smem(L::Q, (int)sizeof(T), XT);
     if (kind == 3 && smem > 0) smem += tma_bs_smem(L::Q, (int)sizeof(T), XT);
     if (smem == 0 || smem > 227 * 1024 || a.stages > 8) return cudaErrorInvalidValue;
@@ -688,13 +689,15 @@ struct TU {
       kern = kind == 0   ? &k_step_tma<L, COLL, S, FORCE, kPack, XT>
              : kind == 1 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, false>
              : kind == 2 ? &k_step_aa_tma<L, COLL, S, FORCE, kPack, XT, true>
-                         : &k_step_tma<L, COLL, S, FORCE, kPack, XT, kPack ? 3 : 0>;
+             : kind == 3 ? &k_step_tma<L, COLL, S, FORCE, kPack, XT, kPack ? 3 : 0>
+                         : &k_step_tma<L, COLL, S, FORCE, kPack, XT, kPack && sizeof(T) == 2 ? 4 : 0>;
       if (kind == 2 || kind == 3) threads = TmaShape<XT, kPack, 1>::kThreads;
+      if (kind == 4) threads = TmaShape<XT, kPack, 0, kPack && sizeof(T) == 2 ? 4 : 0>::kThreads;
     }
     // per instantiation and kind: the shared-memory opt-in (once) and the
     // resident blocks per SM for each ring depth (cached)
-    static bool attr_set[4] = {false, false, false, false};
-    static int per_sm_cache[4][9] = {};
+    static bool attr_set[5] = {false, false, false, false, false};
+    static int per_sm_cache[5][9] = {};
     if (!attr_set[kind]) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       if (e != cudaSuccess) return e;
