@@ -41,9 +41,27 @@ BYTES_PER_NODE = {("D2Q9", "F64"): 144, ("D2Q9", "F32"): 72, ("D2Q9", "F16"): 36
                   ("D3Q19", "F16"): 76, ("D3Q19", "BF16"): 76, ("D3Q27", "F64"): 432,
                   ("D3Q27", "F32"): 216, ("D3Q27", "F16"): 108, ("D3Q27", "BF16"): 108}
 PROFILE = os.path.join(ROOT, "profiles", "stream_collide_d2q9_f32_4096.md")
+# FP64 instructions (DADD + DMUL + DFMA) per node update of the FP64 update, by
+# lattice and collision: ncu counts on D3Q19 128^3 and D2Q9 2048x1024
+# (profiles/stream_collide_d3q19_f64_128.md).  With GB300's 2 FP64 lanes per
+# SM they give the FP64-pipe roofline of the FP64 runs.
+FP64_INSTR_PER_NODE = {("D3Q19", "P_TRT"): 242, ("D3Q19", "TRT_RLB"): 301, ("D3Q19", "TRT"): 192,
+                       ("D2Q9", "P_TRT"): 103, ("D2Q9", "TRT_RLB"): 129, ("D2Q9", "TRT"): 93}
+FP64_LANES_PER_SM = 2
+
+
+def fp64_peak_instr_per_s() -> float:
+    """FP64 instructions per second of the device: SMs x max SM clock x lanes."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = measured_peaks()["sm_max_mhz"]
+    return sms * mhz * 1e6 * FP64_LANES_PER_SM
+
+
 EXTRA_LEGEND = ("d2q9_*: double shear 4096^2 Re=1e5 1/tau-=1.6; d3q19_*/d3q27_*: Taylor-Green "
                 "384^3 Re=1600 Lambda=1/4; collision P-TRT unless named; frac: algorithmic bytes "
-                "/ measured HBM peak; copy: / copy ceiling at the buffer size; v: kernel variant")
+                "/ measured HBM peak; copy: / copy ceiling at the buffer size; alu_frac (FP64): "
+                "FP64 instructions / (SMs x clock x 2 lanes); v: kernel variant")
 
 
 # Device code of the pipelined fused kernel: the committed ncu counters of the
@@ -65,8 +83,9 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured",
+                "sm_max_mhz": float(d.get("sm_max_mhz") or 2070.0)}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
 
 
 def profile_traffic(kernel_hash: str):
@@ -360,6 +379,9 @@ def secondary(lat: str, n: int, storage: str, kind: str, peak: float, collision=
     bpn = BYTES_PER_NODE[(lat, storage)] if scheme == 1 else scheme2_bytes_per_node(lat, storage)
     gbs = bpn * N / dt / 1e9
     out = {"mlups": N / dt / 1e6, "frac": gbs / peak, "v": g.variants()[g.variant]}
+    if storage == "F64" and (lat, collision) in FP64_INSTR_PER_NODE:
+        out["bound"] = "alu"
+        out["alu_frac"] = N / dt * FP64_INSTR_PER_NODE[(lat, collision)] / fp64_peak_instr_per_s()
     if scheme == 2:
         out["bytes_per_node"] = bpn
     rc, _ = g.status()
@@ -1129,7 +1151,8 @@ def run_ours(args):
     d3 = {k[6:] or "F32": extra[k] for k in ("d3q19_f32", "d3q19_f16", "d3q19_bf16", "d3q19_f64",
                                            "d3q19_f32_aa") if k in extra}
     if d3:
-        d3 = {k.upper(): {f: v.get(f) for f in ("mlups", "frac", "copy")} for k, v in d3.items()}
+        d3 = {k.upper(): {f: v.get(f) for f in ("mlups", "frac", "copy", "alu_frac") if f in v}
+              for k, v in d3.items()}
         if "F16" in d3 and d3["F16"]["mlups"] and d3.get("F32", {}).get("mlups"):
             d3["f16_over_f32"] = d3["F16"]["mlups"] / d3["F32"]["mlups"]
         line["d3q19_384"] = compact(dict(workload="D3Q19 P-TRT Taylor-Green 384^3, Re=1600, A/B "
