@@ -337,47 +337,83 @@ __global__ void __launch_bounds__(TmaShape<XT, PACK, ODD ? 1 : 0>::kThreads,
       bool tend = false;
 #pragma unroll
       for (int n = 0; n < NPT; ++n) tend |= act[n] && (jn[n] == 0 || jn[n] == wdt - 1);
+      if (!anywall && wdt == XT) {
+        // no destination row lies beyond a wall (that needs a wall row) and
+        // every node exists: fixed offsets, no per-plane test
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        if constexpr (PACK) {
-          out[0] = g[i].x;
-          out[NPT - 1] = g[i].y;
-        } else {
-          out[0] = g[i];
-        }
-        const int ex = L::cx(i);
-        const long long dy = L::cy(i) == 1 ? yp : (L::cy(i) == -1 ? ym : 0);
-        const long long dz = L::cz(i) == 1 ? zp : (L::cz(i) == -1 ? zm : 0);
-        const bool rw = dy == kWall || dz == kWall;
-        T* orow = ostage + i * SLOT + HT;
-        bool staged = false;
-        if constexpr (ADJ) {
-          if (ex == 0) {  // the pair's word, 4-byte aligned (HT and jn[0] even)
-            if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(orow + jn[0]) = S::enc2(out[0], out[NPT - 1]);
-            else if (act[0]) orow[jn[0]] = S::enc(out[0]);
-            staged = true;
+        for (int i = 0; i < L::Q; ++i) {
+          T* orow = ostage + i * SLOT + HT + L::cx(i);
+          if constexpr (ADJ) {
+            if (L::cx(i) == 0) {
+              *reinterpret_cast<uint32_t*>(orow + jn[0]) = S::enc2(g[i].x, g[i].y);
+            } else {
+              orow[jn[0]] = S::enc(g[i].x);
+              orow[jn[1]] = S::enc(g[i].y);
+            }
+          } else if constexpr (PACK) {
+            orow[jn[0]] = S::enc(g[i].x);
+            orow[jn[1]] = S::enc(g[i].y);
+          } else {
+            orow[jn[0]] = S::enc(g[i]);
           }
         }
-        if (!staged) {
-          const int sh = rw ? 0 : ex;
+      } else {
 #pragma unroll
-          for (int n = 0; n < NPT; ++n)
-            if (act[n]) orow[jn[n] + sh] = S::enc(out[n]);
+        for (int i = 0; i < L::Q; ++i) {
+          if constexpr (PACK) {
+            out[0] = g[i].x;
+            out[NPT - 1] = g[i].y;
+          } else {
+            out[0] = g[i];
+          }
+          const int ex = L::cx(i);
+          const long long dy = L::cy(i) == 1 ? yp : (L::cy(i) == -1 ? ym : 0);
+          const long long dz = L::cz(i) == 1 ? zp : (L::cz(i) == -1 ? zm : 0);
+          const bool rw = dy == kWall || dz == kWall;
+          T* orow = ostage + i * SLOT + HT;
+          bool staged = false;
+          if constexpr (ADJ) {
+            if (ex == 0) {  // the pair's word, 4-byte aligned (HT and jn[0] even)
+              if (act[NPT - 1]) *reinterpret_cast<uint32_t*>(orow + jn[0]) = S::enc2(out[0], out[NPT - 1]);
+              else if (act[0]) orow[jn[0]] = S::enc(out[0]);
+              staged = true;
+            }
+          }
+          if (!staged) {
+            const int sh = rw ? 0 : ex;
+#pragma unroll
+            for (int n = 0; n < NPT; ++n)
+              if (act[n]) orow[jn[n] + sh] = S::enc(out[n]);
+          }
         }
-        if (ex != 0) {
-          if (tend && !rw) {
+      }
+      // a thread that holds the tile's first or last node may have values for
+      // outside the tile's window or the row (wraps, x walls): stored directly
+      if (tend) {
 #pragma unroll
-            for (int n = 0; n < NPT; ++n) {
-              const int x = x0 + jn[n];
-              const int xd = x + ex;
-              if (!act[n] || (xd >= x0 && xd < min(x0 + XT, G.nx))) continue;
-              if (xd >= 0 && xd < G.nx) {
-                buf[i * G.plane + own + dy + dz + xd] = S::enc(out[n]);  // next / previous tile's window
-              } else if (G.per[0]) {
-                buf[i * G.plane + own + dy + dz + (xd < 0 ? xd + G.nx : xd - G.nx)] = S::enc(out[n]);
-              } else {
-                buf[L::opp(i) * G.plane + own + x] = S::enc(out[n]);  // x wall: own opposite slot
-              }
+        for (int i = 0; i < L::Q; ++i) {
+          const int ex = L::cx(i);
+          if (ex == 0) continue;
+          if constexpr (PACK) {
+            out[0] = g[i].x;
+            out[NPT - 1] = g[i].y;
+          } else {
+            out[0] = g[i];
+          }
+          const long long dy = L::cy(i) == 1 ? yp : (L::cy(i) == -1 ? ym : 0);
+          const long long dz = L::cz(i) == 1 ? zp : (L::cz(i) == -1 ? zm : 0);
+          if (dy == kWall || dz == kWall) continue;
+#pragma unroll
+          for (int n = 0; n < NPT; ++n) {
+            const int x = x0 + jn[n];
+            const int xd = x + ex;
+            if (!act[n] || (xd >= x0 && xd < min(x0 + XT, G.nx))) continue;
+            if (xd >= 0 && xd < G.nx) {
+              buf[i * G.plane + own + dy + dz + xd] = S::enc(out[n]);  // next / previous tile's window
+            } else if (G.per[0]) {
+              buf[i * G.plane + own + dy + dz + (xd < 0 ? xd + G.nx : xd - G.nx)] = S::enc(out[n]);
+            } else {
+              buf[L::opp(i) * G.plane + own + x] = S::enc(out[n]);  // x wall: own opposite slot
             }
           }
         }
