@@ -302,7 +302,9 @@ int lbm_set_wait_limit(lbm_ctx* ctx, double seconds, int test_extra_bytes);
 const char* lbm_last_error(void);
 
 /* Kernel variants (nodes per thread, block shape) available for this context,
- * their names, the selected one, and selection by index. */
+ * their names, the selected one, and selection by index.  lbm_set_variant runs
+ * every step with the chosen variant; on the AA layout lbm_autotune may choose
+ * another for the odd steps (lbm_get_variant reports the even steps' one). */
 int lbm_variant_count(const lbm_ctx* ctx, int* n);
 int lbm_variant_name(const lbm_ctx* ctx, int v, char* buf, size_t len);
 int lbm_get_variant(const lbm_ctx* ctx, int* v);
@@ -314,7 +316,9 @@ int lbm_set_variant(lbm_ctx* ctx, int v);
  * is not changed (trial steps read the current buffer and write the other one,
  * which the next step overwrites).  AA layout: there is no spare buffer, so the
  * trials are real steps in pairs (even, odd): the lattice advances by
- * 2 (reps + 1) steps per variant and the step counter with it.  Results are
+ * 2 (reps + 1) or 2 reps + 3 steps per variant and the step counter with it;
+ * the even and odd steps are different kernels and each gets its own fastest
+ * variant (times_ms then holds the mean of the two per variant).  Results are
  * cached per (lattice, storage, collision, mask, extent, layout, forcing
  * scheme) for the process; a cached answer (times_ms NULL) runs nothing.
  * Under forcing scheme 2 the trials are scheme-2 steps.  Synchronises. */

@@ -197,6 +197,7 @@ struct lbm_ctx {
   long long launches = 0;
   std::vector<Variant> vars;
   int var = 0;
+  int var_odd = -1;   // AA: variant of the odd steps when tuned apart (-1: var)
   int sms = 0;
   OpenBC open{};  // open boundaries of the square-cylinder benchmark (off by default)
   bool fresh = true;  // the state was written directly (not yet streamed)
@@ -280,6 +281,7 @@ int ctx_bind(lbm_ctx* c, void* a, void* b, const uint8_t* mask, void* scratch) {
   c->t = 0;
   c->vars = variants_for(c->pl, c->ops, mask != nullptr);
   c->var = default_variant(c->pl, c->vars);
+  c->var_odd = -1;
   return LBM_OK;
 }
 
@@ -293,7 +295,9 @@ int reset_flag(lbm_ctx* c) {
 
 int ctx_step(lbm_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
-    StepLaunch sl = step_of(c, c->vars[c->var]);
+    const bool odd_own = c->pl.p.layout == LBM_LAYOUT_AA && (c->t & 1) && c->var_odd >= 0 &&
+                         c->var_odd < (int)c->vars.size();
+    StepLaunch sl = step_of(c, c->vars[odd_own ? c->var_odd : c->var]);
     cudaError_t e = c->ops->step(sl);
     c->launches += c->scheme == 2 ? 2 : 1;
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "stream-collide launch", e);
@@ -688,6 +692,7 @@ int lbm_get_variant(const lbm_ctx* c, int* v) {
 int lbm_set_variant(lbm_ctx* c, int v) {
   if (!c || v < 0 || v >= (int)c->vars.size()) return fail(LBM_ERR_ARG, "bad variant");
   c->var = v;
+  c->var_odd = -1;
   return LBM_OK;
 }
 
@@ -697,15 +702,17 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   const bool aa = c->pl.p.layout == LBM_LAYOUT_AA;
   using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int>;
   static std::mutex mu;
-  static std::map<Key, int> cache;
+  static std::map<Key, std::pair<int, int>> cache;  // (variant, AA odd-step variant or -1)
   const Key key{c->pl.p.lattice, c->pl.p.storage, c->pl.kernel_collision, c->mask != nullptr,
                 c->pl.p.nx,      c->pl.p.ny,      c->pl.p.nz,            c->pl.g.per[0],
                 c->pl.g.per[1],  c->pl.g.per[2],  c->pl.p.layout,        c->scheme};
   if (!times_ms) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
-    if (it != cache.end() && it->second < (int)c->vars.size()) {
-      c->var = it->second;
+    if (it != cache.end() && it->second.first < (int)c->vars.size() &&
+        it->second.second < (int)c->vars.size()) {
+      c->var = it->second.first;
+      c->var_odd = it->second.second;
       if (chosen) *chosen = c->var;
       return LBM_OK;
     }
@@ -720,24 +727,58 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   }
   int best = c->var;
   float best_ms = 1e30f;
-  const int keep = c->var;
+  const int keep = c->var, keep_odd = c->var_odd;
+  // AA: the even and odd steps are different kernels; each gets its fastest
+  // variant (timed on steps that really advance the lattice)
+  int best_even = c->var, best_odd = c->var;
+  float best_even_ms = 1e30f, best_odd_ms = 1e30f;
+  cudaEvent_t e2 = nullptr;
+  if (aa) rc = cuda_check(cudaEventCreate(&e2), "event");
+  c->var_odd = -1;
   for (int v = 0; v < (int)c->vars.size() && rc == LBM_OK; ++v) {
     cudaError_t e = cudaSuccess;
-    if (!aa) {
+    if (aa) {
+      c->var = v;
+      rc = ctx_step(c, (c->t & 1) ? 3 : 2);  // warm up, end on an even step count
+      if (rc) break;
+      float even_ms = 0.f, odd_ms = 0.f;
+      for (int r = 0; r < reps && e == cudaSuccess && rc == LBM_OK; ++r) {
+        e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) rc = ctx_step(c, 1);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess && rc == LBM_OK) rc = ctx_step(c, 1);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(e2, c->stream);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventSynchronize(e2);
+        float a = 0.f, b = 0.f;
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&a, e0, e1);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&b, e1, e2);
+        even_ms += a;
+        odd_ms += b;
+      }
+      if (rc) break;
+      if (e != cudaSuccess) {
+        rc = fail(LBM_ERR_CUDA, "autotune", e);
+        break;
+      }
+      even_ms /= reps;
+      odd_ms /= reps;
+      if (times_ms) times_ms[v] = 0.5f * (even_ms + odd_ms);
+      if (even_ms < best_even_ms) {
+        best_even_ms = even_ms;
+        best_even = v;
+      }
+      if (odd_ms < best_odd_ms) {
+        best_odd_ms = odd_ms;
+        best_odd = v;
+      }
+      continue;
+    }
+    {
       StepLaunch sl = step_of(c, c->vars[v]);  // reads the state, writes the other buffer
       e = c->ops->step(sl);
       c->launches += (1 + reps) * (c->scheme == 2 ? 2 : 1);
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
       for (int r = 0; r < reps && e == cudaSuccess; ++r) e = c->ops->step(sl);
-    } else {
-      // in place there is no spare buffer: time pairs of (even, odd) steps that
-      // really advance the lattice
-      c->var = v;
-      rc = ctx_step(c, 2);
-      if (rc) break;
-      e = cudaEventRecord(e0, c->stream);
-      if (e == cudaSuccess) rc = ctx_step(c, 2 * reps);
-      if (rc) break;
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -747,7 +788,7 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
       rc = fail(LBM_ERR_CUDA, "autotune", e);
       break;
     }
-    ms /= aa ? 2 * reps : reps;
+    ms /= reps;
     if (times_ms) times_ms[v] = ms;
     if (ms < best_ms) {
       best_ms = ms;
@@ -756,14 +797,20 @@ int lbm_autotune(lbm_ctx* c, int reps, int* chosen, float* times_ms) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (e2) cudaEventDestroy(e2);
   if (rc) {
     c->var = keep;
+    c->var_odd = keep_odd;
     return rc;
+  }
+  if (aa) {
+    best = best_even;
+    c->var_odd = best_odd;
   }
   c->var = best;
   {
     std::lock_guard<std::mutex> lk(mu);
-    cache[key] = best;
+    cache[key] = {best, c->var_odd};
   }
   if (chosen) *chosen = best;
   return LBM_OK;

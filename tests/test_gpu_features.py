@@ -216,8 +216,9 @@ def test_autotune_keeps_state_and_picks_a_variant():
 
 def test_autotune_aa_advances_in_steps_and_stays_consistent():
     """In place the trials are real (even, odd) step pairs: the lattice advances
-    by 2 (reps + 1) steps per variant, and the state equals an A/B run of the
-    same total length."""
+    by 2 (reps + 1) steps per variant (one more for the first when the count
+    starts odd), the even and odd steps may keep different variants, and the
+    state equals an A/B run of the same total length."""
     shape = (1, 32, 128)
     rng = np.random.default_rng(37)
     rho, u = W.random_macros(shape, 2, rng)
@@ -227,8 +228,8 @@ def test_autotune_aa_advances_in_steps_and_stays_consistent():
     nvar = len(g.variants())
     chosen, times = g.autotune(reps=2)
     assert 0 <= chosen < nvar and g.variant == chosen and all(t > 0 for t in times)
-    assert g.t == 1 + nvar * 2 * 3
-    g.step(1)
+    assert g.t == 2 + nvar * 2 * 3
+    g.step(3)  # odd and even steps with their own variants
     ref = gpu_lattice(O.D2Q9, shape, O.TRT, 0.03, 0.25, storage="F32")
     ref.init_equilibrium(rho, u)
     ref.step(g.t)
