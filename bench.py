@@ -1063,6 +1063,16 @@ def run_ours(args):
     e2e_value = e2e_units / e2e_all / 1e6
     h2d = rho_h.numel() * 8 + u_h.numel() * 8
     d2h = rho_o.numel() * 8 + u_o.numel() * 8 + 64
+    # where the end-to-end time goes: the host-link copies of one step, each
+    # timed alone (both calls synchronise; the init / macros kernels included)
+    t0 = time.perf_counter()
+    g.init_equilibrium_host_ptr(rho_h.data_ptr(), u_h.data_ptr())
+    t_h2d = time.perf_counter() - t0
+    g.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.macros_host_ptr(rho_o.data_ptr(), u_o.data_ptr())
+    t_d2h = time.perf_counter() - t0
 
     bpn = BYTES_PER_NODE[("D2Q9", "F32")]
     achieved = bpn * N / kernel_s / 1e9
@@ -1135,7 +1145,8 @@ def run_ours(args):
                                                              ceiling["torch_copy_gbs"])
                                               if ceiling else None)},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "h2d_gbs": h2d / t_h2d / 1e9,
+                "d2h_gbs": (d2h - 64) / t_d2h / 1e9},
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
