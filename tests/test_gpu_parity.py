@@ -164,6 +164,7 @@ def test_all_variants_bit_identical(lat, shape, storage):
     (O.D2Q9, (1, 9, 66), "F64", (0, 0, 1), (1e-5, 0.0, 0.0)),     # FP64 (unpacked), closed box
     (O.D3Q19, (5, 7, 40), "F32", (1, 0, 0), (1e-5, 0.0, 2e-5)),   # y and z walls
     (O.D3Q19, (4, 6, 48), "BF16", (0, 1, 1), (0.0, 0.0, 0.0)),
+    (O.D3Q19, (3, 5, 528), "F16", (1, 0, 1), (1e-5, 0.0, 0.0)),   # full and ragged 16-bit tiles
 ])
 def test_pipelined_variants_match_register_variants(lat, shape, storage, periodic, force):
     """The bulk-copy pipelined kernel (every tile width and ring depth) computes
