@@ -10,13 +10,22 @@
 // or (ibar, x) when x + e_i is beyond one.  Per plane and tile that is one
 // source row, (y - e_iy, z - e_iz) of plane ibar (or the own row of plane i at a
 // wall), copied with the 16-byte halo exactly like the A/B pull, and one
-// destination row, (y + e_iy, z + e_iz) of plane i shifted by e_ix.
+// destination row, (y + e_iy, z + e_iz) of plane i shifted by e_ix.  Stored
+// thread by thread, such a shifted row makes every warp store span two
+// 128-byte lines, so the odd step stages the tile's destination rows in shared
+// memory (row i holds destination x at element HT + x - x0) and a store warp
+// (warp 1) writes each row's 16-byte aligned interior with one bulk
+// shared-to-global copy and its few end elements one by one.  Values that
+// leave the tile's window (the neighbour tile's first or last slot), wrap
+// across a periodic row end or bounce at an x wall are stored directly by the
+// consumer thread that holds the tile's first or last node.
 //
 // In place is race free: the slots node x reads in a step are exactly the slots
 // it writes (its own set, disjoint from every other node's), every one of them
-// has landed in shared memory before the node's consumer stores, and the halo
-// elements a copy brings along that belong to other nodes are never used.
-// Masked lattices use the register kernels of aa.cuh.
+// has landed in shared memory before the node's values are stored (by its
+// consumer or the store warp), and the halo elements a copy brings along that
+// belong to other nodes are never used.  Masked lattices use the register
+// kernels of aa.cuh.
 #pragma once
 #include "aa.cuh"
 #include "dispatch.h"
