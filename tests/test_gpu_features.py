@@ -45,6 +45,8 @@ def test_aa_layout_matches_ab_bitwise(lat, shape, storage, steps):
     (O.D2Q9, (1, 9, 66), "F64", (0, 0, 1), (1e-5, 0.0, 0.0)),     # FP64, closed box
     (O.D3Q19, (5, 7, 40), "F32", (1, 0, 0), (1e-5, 0.0, 2e-5)),   # y and z walls
     (O.D3Q19, (4, 6, 48), "BF16", (0, 1, 1), (0.0, 0.0, 0.0)),
+    (O.D3Q19, (3, 5, 528), "F32", (1, 0, 1), (1e-5, 0.0, 0.0)),   # full and ragged tiles, y walls
+    (O.D3Q19, (3, 4, 528), "F16", (1, 1, 0), (0.0, 0.0, 0.0)),    # full 16-bit tiles, z walls
 ])
 def test_aa_pipelined_variants_match_ab(lat, shape, storage, periodic, force):
     """Every variant of the in-place AA update (pipelined and register) gives the
