@@ -146,8 +146,11 @@ int lbm_bind_buffers(lbm_ctx* ctx, void* pop_a, void* pop_b, const uint8_t* soli
  * counter to 0.  rho: device FP64 [N]; u: device FP64 [D][N]. */
 int lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u);
 
-/* As lbm_init_equilibrium with HOST inputs; copies them through the scratch
- * buffer and synchronises the stream before returning. */
+/* As lbm_init_equilibrium with HOST inputs; synchronises the stream before
+ * returning.  Page-locked buffers mapped into the device's address space
+ * (cudaHostAlloc, cudaHostRegister, torch pin_memory) are read in place by the
+ * init kernel over the host link; other host memory is copied through the
+ * scratch buffer first. */
 int lbm_init_equilibrium_host(lbm_ctx* ctx, const double* rho, const double* u);
 
 /* Advances n >= 0 time steps (the hot path).  Asynchronous; returns launch
@@ -159,7 +162,9 @@ int lbm_step(lbm_ctx* ctx, int n);
  * state into device FP64 buffers rho [N] and u [D][N].  Solid nodes get rho0, 0. */
 int lbm_macros(lbm_ctx* ctx, double* rho, double* u);
 
-/* As lbm_macros into HOST buffers; synchronises the stream. */
+/* As lbm_macros into HOST buffers; synchronises the stream.  Page-locked,
+ * mapped buffers are written in place by the macros kernel; other host memory
+ * receives a copy from the scratch buffer. */
 int lbm_macros_host(lbm_ctx* ctx, double* rho, double* u);
 
 /* Decoded FP64 pre-collision populations f [Q][N] (device).  Solid nodes: w_i rho0. */

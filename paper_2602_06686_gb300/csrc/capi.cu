@@ -408,9 +408,29 @@ int lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) {
   return cuda_check(e, "init equilibrium");
 }
 
+// Device address of a host buffer the kernels can use in place: page-locked
+// memory registered with CUDA and mapped into the device's address space
+// (cudaHostAlloc / cudaHostRegister under unified addressing), else NULL.
+static const void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is not an error here
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int lbm_init_equilibrium_host(lbm_ctx* c, const double* rho, const double* u) {
   CHECK_CTX(c);
   if (!rho || !u) return fail(LBM_ERR_ARG, "rho and u are required");
+  const void* mr = mapped_host(rho);
+  const void* mu = mapped_host(u);
+  if (mr && mu) {
+    // page-locked, mapped buffers: the init kernel reads them over the host link
+    int rc = lbm_init_equilibrium(c, static_cast<const double*>(mr), static_cast<const double*>(mu));
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  }
   double* fr = reinterpret_cast<double*>(c->scratch + c->pl.field_off);
   double* fu = fr + c->pl.N;
   const size_t nb = (size_t)c->pl.N * sizeof(double);
@@ -441,6 +461,15 @@ int lbm_macros(lbm_ctx* c, double* rho, double* u) {
 int lbm_macros_host(lbm_ctx* c, double* rho, double* u) {
   CHECK_CTX(c);
   if (!rho || !u) return fail(LBM_ERR_ARG, "rho and u are required");
+  const void* mr = mapped_host(rho);
+  const void* mu = mapped_host(u);
+  if (mr && mu) {
+    // page-locked, mapped buffers: the macros kernel writes them over the host link
+    int rc = lbm_macros(c, static_cast<double*>(const_cast<void*>(mr)),
+                        static_cast<double*>(const_cast<void*>(mu)));
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  }
   double* fr = reinterpret_cast<double*>(c->scratch + c->pl.field_off);
   double* fu = fr + c->pl.N;
   int rc = lbm_macros(c, fr, fu);
