@@ -318,7 +318,9 @@ __device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R
 // short of consumer warps (occupancy, not registers, limits it).
 // With the staged bulk stores (MODE 3, one more warp) 16-bit storage asks for
 // 3: at 4 blocks of 256 threads the 64-register cap spills.  Four nodes per
-// thread (MODE 4) hold two pairs of populations and ask for 3 as well.
+// thread (MODE 4) hold two pairs of populations and keep the 16-bit request
+// of 4 (D3Q19 at tile 384: 128 threads, 128 registers, no spill); on D3Q27
+// they keep its 3 (166 registers).
 template <class L, class S, int MODE = 0>
 constexpr int tma_min_blocks() {
   if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : 3;
