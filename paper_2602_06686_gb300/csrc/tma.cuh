@@ -320,10 +320,12 @@ __device__ __forceinline__ R phi_grad(const Geo& G, const uint8_t* mask, const R
 // 3: at 4 blocks of 256 threads the 64-register cap spills.  Four nodes per
 // thread (MODE 4) hold two pairs of populations and keep the 16-bit request
 // of 4 (D3Q19 at tile 384: 128 threads, 128 registers, no spill); on D3Q27
-// they keep its 3 (166 registers).
-template <class L, class S, int MODE = 0>
+// they keep its 3 (166 registers).  D3Q27 tiles wider than 256 with two nodes
+// per thread (224 threads and more) ask for 2: three would cap them at 97
+// registers and spill.
+template <class L, class S, int MODE = 0, int XT = 0>
 constexpr int tma_min_blocks() {
-  if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : 3;
+  if (L::Q == 27) return sizeof(typename S::T) == 8 ? 1 : (XT > 256 && MODE != 4 ? 2 : 3);
   if (MODE == 3 && sizeof(typename S::T) == 2) return 3;
   if (MODE == 4 && sizeof(typename S::T) == 2) return 4;
   return sizeof(typename S::T) == 2 ? 4 : (sizeof(typename S::T) == 4 ? 2 : 1);
@@ -331,7 +333,7 @@ constexpr int tma_min_blocks() {
 
 template <class L, int COLL, class S, bool FORCE, bool PACK, int XT, int MODE = 0>
 __global__ void __launch_bounds__(TmaShape<XT, PACK, MODE == 3 ? 1 : 0, MODE == 4 ? 4 : 0>::kThreads,
-                                  tma_min_blocks<L, S, MODE>())
+                                  tma_min_blocks<L, S, MODE, XT>())
     k_step_tma(const TmaArgs<typename S::R> a) {
   using T = typename S::T;
   using R = typename S::R;

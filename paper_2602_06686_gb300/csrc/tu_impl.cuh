@@ -634,12 +634,12 @@ struct TU {
   // flight per thread already)
   static constexpr int kMaxNV = L::Q == 27 ? 2 : 8;
   static constexpr int kTile27 = kPack ? 256 : 128;
-  // 16-bit D3Q27 also offers 384.  Where nx is a multiple of 384 (the 384^3
+  // Packed D3Q27 also offers 384.  Where nx is a multiple of 384 (the 384^3
   // Taylor-Green) 256-wide tiles leave every second tile of a row half empty,
   // a quarter of the consumer threads idle, and the four-node FP16 update is
   // bound by its consumer warps (166 registers each), not by bytes: 384-wide
-  // tiles ran it at 0.87 of the copy peak against 0.67 on GB300.
-  static constexpr bool kWide27 = kOneTile && kPack && sizeof(T) == 2;
+  // tiles ran it at 0.87 of the measured HBM peak against 0.67 on GB300.
+  static constexpr bool kWide27 = kOneTile && kPack;
   static bool tma_width_ok(int X) {
     if (kOneTile) return X == kTile27 || (kWide27 && X == 384);
     return kPack ? (X == 256 || X == 384 || X == 512) : (X == 128 || X == 192 || X == 256);
