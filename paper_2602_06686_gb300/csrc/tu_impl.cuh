@@ -627,8 +627,8 @@ struct TU {
 
   // ---- pipelined bulk-copy kernel (kind 1)
   static constexpr bool kPack = sizeof(R) == 4;
-  // D3Q27 keeps one tile width (256 packed, 128 FP64): its 27-plane kernels
-  // are the slowest to compile, and the width sweep gains little there.
+  // D3Q27 compiles fewer tile widths (256 and 384 packed, 128 FP64): its
+  // 27-plane kernels are the slowest to compile.
   static constexpr bool kOneTile = L::Q == 27;
   // register kernels: at most 2 nodes per thread on D3Q27 (54 populations in
   // flight per thread already)
@@ -638,7 +638,8 @@ struct TU {
   // Taylor-Green) 256-wide tiles leave every second tile of a row half empty,
   // a quarter of the consumer threads idle, and the four-node FP16 update is
   // bound by its consumer warps (166 registers each), not by bytes: 384-wide
-  // tiles ran it at 0.87 of the measured HBM peak against 0.67 on GB300.
+  // tiles ran it at 0.87 of the measured HBM peak against 0.67 on GB300
+  // (FP32, closer to its bytes: 0.90 against 0.88).
   static constexpr bool kWide27 = kOneTile && kPack;
   static bool tma_width_ok(int X) {
     if (kOneTile) return X == kTile27 || (kWide27 && X == 384);
