@@ -52,6 +52,8 @@
  *     unless a call says it synchronises.
  *   - Return value: LBM_OK (0) or a negative LBM_ERR_* code; nothing is thrown
  *     across the ABI and nothing exits the process.  lbm_strerror names a code.
+ *     A NULL context, batch, parameter block or required output pointer is
+ *     LBM_ERR_ARG, found before any CUDA call.
  *   - The time level: after lbm_init_equilibrium / lbm_set_populations and any
  *     number of lbm_step calls, lbm_macros and lbm_get_populations describe the
  *     pre-collision state f(x, t).
@@ -329,6 +331,8 @@ int lbm_set_variant(lbm_ctx* ctx, int v);
  * Under forcing scheme 2 the trials are scheme-2 steps.  Synchronises. */
 int lbm_autotune(lbm_ctx* ctx, int reps, int* chosen, float* times_ms);
 
+/* Frees the context (not the bound buffers); NULL is a no-op (LBM_OK).  A
+ * lattice view of a batch is LBM_ERR_STATE: lbm_batch_destroy frees it. */
 int lbm_destroy(lbm_ctx* ctx);
 
 /* Streaming copy kernel (128-bit loads/stores, grid-stride) of `bytes` from
@@ -382,6 +386,7 @@ int lbm_batch_set_barrier(lbm_batch* b, double timeout_s, int extra);
 /* Number of kernel launches the last lbm_batch_step enqueued. */
 int lbm_batch_launches(const lbm_batch* b, long long* launches);
 
+/* Frees the batch and its lattice views; NULL is a no-op (LBM_OK). */
 int lbm_batch_destroy(lbm_batch* b);
 
 #ifdef __cplusplus

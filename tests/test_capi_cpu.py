@@ -76,3 +76,66 @@ def test_invalid_parameters_rejected(lib, kw):
     with pytest.raises(LBMError) as e:
         buffer_sizes(make_params(**base))
     assert e.value.code == -1
+
+
+def test_null_handles_and_outputs_are_argument_errors():
+    """Every entry point given a NULL context, batch, parameter block or
+    required output returns LBM_ERR_ARG before any CUDA call (this machine may
+    have no GPU); destroying NULL is a no-op."""
+    import ctypes
+
+    from paper_2602_06686_gb300 import build
+    raw = ctypes.CDLL(build.build())  # no argtypes: every argument spelled out
+    d, sz, ll = ctypes.c_double, ctypes.c_size_t, ctypes.c_longlong
+    calls = {
+        "lbm_buffer_sizes": (None, None, None),
+        "lbm_create": (None, None, None),
+        "lbm_bind_buffers": (None, None, None, None, None),
+        "lbm_init_equilibrium": (None, None, None),
+        "lbm_init_equilibrium_host": (None, None, None),
+        "lbm_step": (None, 1),
+        "lbm_macros": (None, None, None),
+        "lbm_macros_host": (None, None, None),
+        "lbm_get_populations": (None, None),
+        "lbm_set_populations": (None, None),
+        "lbm_diagnostics": (None, None),
+        "lbm_velocity_l2": (None, None, None),
+        "lbm_set_open_boundaries": (None, d(0.01), d(1.0)),
+        "lbm_set_forcing_scheme": (None, 2),
+        "lbm_momentum_exchange": (None, None),
+        "lbm_status": (None, None),
+        "lbm_diagnostics_noalloc": (None, None, None, None, ll(0), None, None),
+        "lbm_step_count": (None, None),
+        "lbm_checkpoint": (None, None, sz(0), None),
+        "lbm_restore": (None, None, sz(0), ll(0)),
+        "lbm_launch_count": (None, None),
+        "lbm_set_wait_limit": (None, d(1.0), 0),
+        "lbm_variant_count": (None, None),
+        "lbm_variant_name": (None, 0, None, sz(0)),
+        "lbm_get_variant": (None, None),
+        "lbm_set_variant": (None, 0),
+        "lbm_autotune": (None, 1, None, None),
+        "lbm_copy_ceiling": (None, None, sz(16), None),
+        "lbm_batch_buffer_sizes": (0, None, None, None),
+        "lbm_batch_create": (0, None, None, None),
+        "lbm_batch_bind": (None, None, None, None),
+        "lbm_batch_lattice": (None, 0, None),
+        "lbm_batch_step": (None, 1, 0),
+        "lbm_batch_variant_count": (None, None),
+        "lbm_batch_variant_name": (None, 0, None, sz(0)),
+        "lbm_batch_set_variant": (None, 0),
+        "lbm_batch_autotune": (None, 1, None, None),
+        "lbm_batch_set_barrier": (None, d(1.0), 0),
+        "lbm_batch_launches": (None, None),
+    }
+    raw.lbm_last_error.restype = ctypes.c_char_p
+    for name, args in calls.items():
+        assert getattr(raw, name)(*args) == -1, name
+        assert raw.lbm_last_error(), name
+    assert raw.lbm_destroy(None) == 0
+    assert raw.lbm_batch_destroy(None) == 0
+    # every entry point that takes a handle or a parameter block is covered
+    takes_handle = {n for n in _declared()
+                    if n not in ("lbm_version", "lbm_strerror", "lbm_last_error",
+                                 "lbm_destroy", "lbm_batch_destroy")}
+    assert takes_handle == set(calls)
