@@ -44,7 +44,9 @@
  *     (bound with lbm_bind_buffers); the library never allocates device memory.
  *     It allocates only its host-side context.
  *   - "device" pointers must be addresses in the current CUDA device's memory
- *     (or managed memory); "host" pointers are ordinary host memory.
+ *     (or managed memory); "host" pointers are ordinary host memory.  Device
+ *     FP64 fields must be 8-byte aligned (else LBM_ERR_ALIGN, before any
+ *     launch); host fields of any alignment are accepted.
  *   - Field layout: scalar fields are [nz][ny][nx] (x fastest, no padding),
  *     vector fields are D consecutive scalar fields (component planes), and
  *     decoded populations are Q consecutive scalar fields, all FP64.

@@ -395,9 +395,14 @@ int lbm_bind_buffers(lbm_ctx* c, void* pop_a, void* pop_b, const uint8_t* solid_
   return ctx_bind(c, pop_a, pop_b, solid_mask, scratch);
 }
 
+// FP64 fields are read and written element by element by the kernels: a
+// device pointer that is not 8-byte aligned is refused before any launch.
+static bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
 int lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) {
   CHECK_CTX(c);
   if (!rho || !u) return fail(LBM_ERR_ARG, "rho and u are required");
+  if (!aligned8(rho) || !aligned8(u)) return fail(LBM_ERR_ALIGN, "rho and u must be 8-byte aligned");
   c->cur = 0;
   c->t = 0;
   c->fresh = true;
@@ -410,8 +415,10 @@ int lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) {
 
 // Device address of a host buffer the kernels can use in place: page-locked
 // memory registered with CUDA and mapped into the device's address space
-// (cudaHostAlloc / cudaHostRegister under unified addressing), else NULL.
+// (cudaHostAlloc / cudaHostRegister under unified addressing) and 8-byte
+// aligned, else NULL (the caller then copies through the scratch buffer).
 static const void* mapped_host(const void* p) {
+  if (!aligned8(p)) return nullptr;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();  // an unregistered pointer is not an error here
@@ -453,6 +460,7 @@ int lbm_step(lbm_ctx* c, int n) {
 int lbm_macros(lbm_ctx* c, double* rho, double* u) {
   CHECK_CTX(c);
   if (!rho || !u) return fail(LBM_ERR_ARG, "rho and u are required");
+  if (!aligned8(rho) || !aligned8(u)) return fail(LBM_ERR_ALIGN, "rho and u must be 8-byte aligned");
   cudaError_t e = c->ops->macros(aux_of(c), rho, u);
   ++c->launches;
   return cuda_check(e, "macros");
@@ -485,6 +493,7 @@ int lbm_macros_host(lbm_ctx* c, double* rho, double* u) {
 int lbm_get_populations(lbm_ctx* c, double* f) {
   CHECK_CTX(c);
   if (!f) return fail(LBM_ERR_ARG, "f is NULL");
+  if (!aligned8(f)) return fail(LBM_ERR_ALIGN, "f must be 8-byte aligned");
   cudaError_t e = c->ops->get_pop(aux_of(c), f);
   ++c->launches;
   return cuda_check(e, "get populations");
@@ -493,6 +502,7 @@ int lbm_get_populations(lbm_ctx* c, double* f) {
 int lbm_set_populations(lbm_ctx* c, const double* f) {
   CHECK_CTX(c);
   if (!f) return fail(LBM_ERR_ARG, "f is NULL");
+  if (!aligned8(f)) return fail(LBM_ERR_ALIGN, "f must be 8-byte aligned");
   int rc = reset_flag(c);
   if (rc) return rc;
   c->fresh = true;
@@ -566,6 +576,7 @@ int lbm_diagnostics(lbm_ctx* c, double out[8]) {
 int lbm_velocity_l2(lbm_ctx* c, const double* u_ref, double* out) {
   CHECK_CTX(c);
   if (!u_ref || !out) return fail(LBM_ERR_ARG, "u_ref and out are required");
+  if (!aligned8(u_ref)) return fail(LBM_ERR_ALIGN, "u_ref must be 8-byte aligned");
   double r[8];
   int rc = run_diag(c, u_ref, r);
   if (rc) return rc;
