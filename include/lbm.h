@@ -256,7 +256,9 @@ int lbm_status(lbm_ctx* ctx, long long* first_step);
  * lbm_diagnostics for the state held in `pop_state` and writes them to `out`
  * (device, 8 FP64) asynchronously on `cuda_stream`:
  *   p           the lattice's parameters (as given to lbm_create);
- *   pop_state   device buffer holding the current state: for the A/B layout
+ *   pop_state   device buffer holding the current state (256-byte aligned, as
+ *               for lbm_bind_buffers, and so is solid_mask; out 8-byte aligned;
+ *               else LBM_ERR_ALIGN before any CUDA call): for the A/B layout
  *               the buffer the next step reads (pop_a after an even number of
  *               steps since initialisation, pop_b after an odd one), for AA the
  *               single buffer;

@@ -145,6 +145,11 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* p, const void* pop_stat
   int rc = plan(p, &pl);
   if (rc) return rc;
   if (!pop_state || !out) return ctx_fail(LBM_ERR_ARG, "pop_state and out are required");
+  // the alignment lbm_bind_buffers asks of the state and the mask; out is FP64
+  const uintptr_t ps = reinterpret_cast<uintptr_t>(pop_state);
+  const uintptr_t ms = reinterpret_cast<uintptr_t>(solid_mask);
+  if ((ps & 255u) || (ms & 255u) || (reinterpret_cast<uintptr_t>(out) & 7u))
+    return ctx_fail(LBM_ERR_ALIGN, "pop_state and solid_mask must be 256-byte aligned, out 8-byte");
   if (steps_done < 0) return ctx_fail(LBM_ERR_ARG, "steps_done must be >= 0");
   if (pl.N > kNoAllocMaxNodes) {
     char buf[160];

@@ -139,3 +139,23 @@ def test_null_handles_and_outputs_are_argument_errors():
                     if n not in ("lbm_version", "lbm_strerror", "lbm_last_error",
                                  "lbm_destroy", "lbm_batch_destroy")}
     assert takes_handle == set(calls)
+
+
+def test_noalloc_diagnostics_refuses_misaligned_buffers(lib):
+    """The no-scratch diagnostics checks the alignment lbm_bind_buffers asks
+    of the state and mask (256 bytes) and of its FP64 output (8 bytes) before
+    any CUDA call; the addresses are never dereferenced here."""
+    import ctypes
+
+    from paper_2602_06686_gb300.lbm import make_params
+    p = make_params("D2Q9", 64, 64, nu=0.01, Lambda=0.25, storage="F32")
+    base = 1 << 20  # a 256-byte aligned address value
+    cases = [(base + 16, None, base), (base, base + 1, base), (base, None, base + 4)]
+    for state, mask, out in cases:
+        rc = lib.lbm_diagnostics_noalloc(ctypes.byref(p), ctypes.c_void_p(state), ctypes.c_void_p(mask),
+                                         None, 0, ctypes.c_void_p(out), None)
+        assert rc == -7, (state, mask, out)
+    # a lattice beyond the static array's capacity is refused first by size
+    big = make_params("D2Q9", 1024, 1024, nu=0.01, Lambda=0.25, storage="F32")
+    assert lib.lbm_diagnostics_noalloc(ctypes.byref(big), ctypes.c_void_p(base), None, None, 0,
+                                       ctypes.c_void_p(base), None) == -1
