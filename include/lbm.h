@@ -77,7 +77,9 @@ extern "C" {
 #define LBM_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
 #define LBM_ERR_UNSUPPORTED (-5) /* valid but not implemented combination */
 #define LBM_ERR_STATE (-6)       /* call out of order (e.g. buffers not bound) */
-#define LBM_ERR_ALIGN (-7)       /* a buffer is not 256-byte aligned */
+#define LBM_ERR_ALIGN (-7)       /* a buffer is not aligned as required: 256 bytes for
+                                    population, mask and scratch buffers, 8 bytes for
+                                    FP64 device fields */
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
 typedef enum {

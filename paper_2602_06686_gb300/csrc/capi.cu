@@ -356,7 +356,7 @@ const char* lbm_strerror(int code) {
     case LBM_ERR_STATE:
       return "call out of order";
     case LBM_ERR_ALIGN:
-      return "buffer not 256-byte aligned";
+      return "buffer not aligned as required (256 bytes; 8 for FP64 fields)";
   }
   return "unknown error";
 }
